@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the crossbar nodal solve on one GB300 (or N independent replicas).
+
+Workload (default ``xbar256_mixed``): a 256 x 256 crossbar (131072 unknowns),
+R_s = R_w = R_b = 1 ohm, R_sense = 10 ohm, G log-uniform in [1e-6, 1e-4] S,
+8192 input vectors uniform in [0, 0.5] V; synthetic, seeded.
+
+One step = one pass of the whole hot path over one batch, through the C ABI:
+    xbar_set_conductances (assembly) -> xbar_factor -> xbar_solve
+in the mixed form (FP32 factor + FP32 substitutions + FP64-residual
+refinement to max |dI|/|I| <= 1e-8).  ``value`` is input vectors solved per
+second (solves/s) over all ranks.  The plain FP64 block-LU path is timed on the
+same GPU in the same run (``fp64_baseline``) and the CPU oracle on the host
+cores (``cpu_baseline``), which also gives the measured error of this run's
+currents.  Phases are timed with CUDA events recorded by the library around
+each kernel launch on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xbar|reference]
+
+Multi-GPU: the path has no exchange step; N ranks run independent replicas
+(each its own map and batch, seed + rank), ``scaling`` = "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s vs plain FP64 block-LU on same GPU at ≤1e-8 rel. current error"
+UNIT = "solves/s"
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="xbar", choices=["xbar", "reference"])
+    ap.add_argument("--workload", default="xbar256_mixed")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=64, help="vectors the CPU oracle substitutes")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Dist:
+    def __init__(self):
+        import torch
+        self.rank, self.world, self.local = dist_env()
+        self.torch = torch
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
+        self.pg.all_reduce(t)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# Peaks of the arithmetic pipes used here, from unit counts and the maximum SM clock of a GB300
+# (152 SMs; 128 FP32 lanes and 2 FP64 FMA per SM per clock); HBM from the measured copy.
+def pipe_peaks(sm_max_mhz=2070.0):
+    clk = sm_max_mhz * 1e6
+    return {"fp32_tflops": 152 * 128 * 2 * clk / 1e12, "fp64_tflops": 152 * 2 * 2 * clk / 1e12}
+
+
+def algorithmic_work(phase, M, N, B):
+    """(amount, unit, bound) of the method's own work for ONE launch of a phase kernel."""
+    if phase == "sweep":          # (2N-1) dense (M x M)(M x B) products
+        return (2 * N - 1) * 2.0 * M * M * B, "flop"
+    if phase == "resid":          # per word-line node and vector: chain fwd (3) + bwd (2) + residual (7)
+        return 12.0 * M * N * B, "flop"
+    if phase == "update":         # w += d (1) and the current dot (2)
+        return 3.0 * M * N * B, "flop"
+    if phase == "factor":         # N inversions of M x M (Gauss-Jordan 2M^3) + Schur formation
+        return N * (2.0 * M ** 3 + 4.0 * M * M), "flop"
+    return 0.0, "flop"
+
+
+# ---------------------------------------------------------------------------------------------
+# the xbar (GPU) arm
+# ---------------------------------------------------------------------------------------------
+def run_xbar(args):
+    import torch
+
+    from paper_2410_19993_gb300 import inputs, xbar
+
+    d = Dist()
+    rank, world, local = d.rank, d.world, d.local
+    torch.cuda.set_device(local)
+    w = inputs.WORKLOADS[args.workload]
+    M, N, B = w.M, w.N, w.B
+    R = w.circuits[0].as_tuple()
+    G, V = inputs.crossbar(M, N, B, seed=w.seed + rank, g_lo=w.g_lo, g_hi=w.g_hi, v_max=w.v_max)
+    stream = torch.cuda.current_stream()
+    Gd = torch.from_numpy(G).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    I64 = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    xb = xbar.Crossbar.assemble(Gd, *R, stream=stream)
+    info_box = {}
+
+    def step_mixed():
+        xb.set_conductances(Gd)
+        xb.factor("fp32_ir")
+        _, info = xb.solve(Vd, I, tol=TOL, max_iter=10)
+        info_box.update(info)
+
+    def step_fp64():
+        xb.set_conductances(Gd)
+        xb.factor("fp64")
+        xb.solve(Vd, I64)
+
+    def timed(fn, K):
+        d.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d.barrier()
+        return e0.elapsed_time(e1) / 1e3
+
+    for _ in range(args.warmup):
+        step_mixed()
+    cvd = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    clocks = Clocks(int(cvd[local]) if local < len(cvd) and cvd[local].isdigit() else local)
+    xb.profile_enable(True)
+    clocks.start()
+    t_mixed = timed(step_mixed, args.steps)
+    clk = clocks.stop()
+    prof = xb.profile_read(reset=True)
+    xb.profile_enable(False)
+    t_mixed = d.max(t_mixed)
+    total_solves = d.sum(float(B * args.steps))
+    value = total_solves / t_mixed
+    I_mixed = I.cpu().numpy()
+
+    # plain FP64 block-LU on the same GPU
+    step_fp64()
+    xb.profile_enable(True)
+    t64 = d.max(timed(step_fp64, args.fp64_steps))
+    prof64 = xb.profile_read(reset=True)
+    xb.profile_enable(False)
+    fp64_value = d.sum(float(B * args.fp64_steps)) / t64
+    I_fp64 = I64.cpu().numpy()
+    err_vs_fp64 = float(np.max(np.abs(I_mixed - I_fp64) / np.maximum(np.abs(I_fp64), 1e-300)))
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        Gh = torch.from_numpy(G).pin_memory()
+        Vh = torch.from_numpy(V).pin_memory()
+        Ih = torch.zeros((B, N), dtype=torch.float64).pin_memory()
+
+        def step_e2e():
+            xb.set_conductances(Gh)
+            xb.factor("fp32_ir")
+            xb.solve(Vh, Ih, tol=TOL, max_iter=10)
+
+        step_e2e()
+        d.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        t_e2e = d.max(time.perf_counter() - t0)
+        e2e = {"value": d.sum(float(B * args.steps)) / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(G.nbytes + V.nbytes), "d2h_bytes_per_step": int(B * N * 8),
+               "ms_per_step": 1e3 * t_e2e / args.steps}
+        assert np.array_equal(Ih.numpy(), I_mixed), "host-buffer solve differs from device-buffer solve"
+
+    # per-phase kernel times inside the timed region, and the roofline of the dominant kernel
+    per_step = {ph: {"launches": v["launches"] / args.steps, "ms": v["ms"] / args.steps}
+                for ph, v in prof.items() if v["launches"]}
+    launches = int(sum(v["launches"] for v in prof.values()))
+    dom = max(per_step, key=lambda ph: per_step[ph]["ms"])
+    work, _ = algorithmic_work(dom, M, N, B)
+    ms_launch = prof[dom]["ms"] / prof[dom]["launches"]
+    peaks = pipe_peaks(measured_peaks().get("sm_max_mhz", 2070.0))
+    achieved = work / (ms_launch / 1e3) / 1e12
+    if dom in ("sweep", "factor", "update"):
+        bound, peak, note = "alu", peaks["fp32_tflops"], "FP32 FMA pipe, 152 SM x 128 lanes x 2 x max SM clock"
+    else:
+        bound, peak, note = "alu", peaks["fp64_tflops"], "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock"
+    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_note": note,
+                "work_per_launch": work, "ms_per_launch": ms_launch}
+
+    cpu = None
+    err_vs_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, Iref = cpu_baseline(M, N, G, R, V, args.cpu_sample)
+        err_vs_oracle = float(np.max(np.abs(I_mixed - Iref) / np.abs(Iref)))
+        cpu["fp64_gpu_err_vs_oracle"] = float(np.max(np.abs(I_fp64 - Iref) / np.abs(Iref)))
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refinement", "data": "synthetic",
+        "config": {"workload": args.workload, "M": M, "N": N, "B": B, "R_s": R[0], "R_w": R[1], "R_b": R[2],
+                   "R_sense": R[3], "precision": "fp32 factor+sweeps, fp64 residual/update", "tol": TOL,
+                   "step": "set_conductances + factor + solve (all refinement)",
+                   "l2": "working set per step (>6 GB) exceeds the 129 MB L2", "parallelism": f"replicas{world}"},
+        "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                          "steps": args.fp64_steps,
+                          "phases_ms_per_step": {ph: v["ms"] / args.fp64_steps for ph, v in prof64.items() if v["launches"]}},
+        "speedup_vs_fp64": value / fp64_value,
+        "rel_err_vs_fp64_gpu": err_vs_fp64,
+        "rel_err_vs_oracle": err_vs_oracle,
+        "refinement": {k: info_box.get(k) for k in ("iters", "max_rel_dI", "resid_inf", "err_est")},
+        "phases_per_step": per_step,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    xb.destroy()
+    d.close()
+
+
+def cpu_baseline(M, N, G, R, V, sample):
+    """The oracle as it stands on the host cores: one factorization plus `sample` substitutions."""
+    import oracle
+    B = V.shape[0]
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    f = oracle.factor(M, N, G, *R)
+    t_fac = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.solve_factored(f, V[:sample], nthreads=threads)
+    t_sol = (time.perf_counter() - t0) / sample
+    value = B / (t_fac + B * t_sol)
+    # exact currents of the whole batch by linearity (M unit substitutions)
+    Geff = oracle.transfer_matrix(f, nthreads=threads)
+    return ({"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "sample": f"one banded-LU factorization ({t_fac:.1f} s) + {sample} substitutions "
+                       f"({1e3 * t_sol:.1f} ms each on {threads} threads); value = B/(t_factor + B*t_subst), B={B}"},
+            V @ Geff)
+
+
+# ---------------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle, timed as it stands on the host cores
+# ---------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2410_19993_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    M, N, B = w.M, w.N, w.B
+    R = w.circuits[0].as_tuple()
+    G, V = inputs.crossbar(M, N, B, seed=w.seed, g_lo=w.g_lo, g_hi=w.g_hi, v_max=w.v_max)
+    threads = os.cpu_count() or 1
+    per_step = max(1, min(args.cpu_sample, B))
+    t0 = time.perf_counter()
+    f = oracle.factor(M, N, G, *R)
+    t_fac = time.perf_counter() - t0
+    for k in range(args.warmup):
+        oracle.solve_factored(f, V[(k * per_step) % B:][:per_step], nthreads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.solve_factored(f, V[(k * per_step) % B:][:per_step], nthreads=threads)
+    t_steps = time.perf_counter() - t0
+    t_sol = t_steps / (args.steps * per_step)
+    value = B / (t_fac + B * t_sol)
+    sample = (f"each step substitutes {per_step} vectors; one banded-LU factorization ({t_fac:.1f} s) "
+              f"timed once; value = B/(t_factor + B*t_subst), B={B}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_steps / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "M": M, "N": N, "B": B, "R_s": R[0], "R_w": R[1], "R_b": R[2],
+                   "R_sense": R[3], "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_xbar(args)
+
+
+if __name__ == "__main__":
+    main()

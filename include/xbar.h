@@ -1,0 +1,176 @@
+/*
+ * xbar.h -- C ABI of libxbar, a GB300 (sm_103a) solver for the DC nodal
+ * equations of memristive crossbars with interconnect parasitics, after
+ * XbarSim (Kolinko, Amin, Zand, Bakos, arXiv 2410.19993).
+ *
+ * Problem (Sec. II "Methodology", Sec. II-A "Circuit Model", Eqs. 1-7): an
+ * M x N crossbar has M word lines (rows i) and N bit lines (columns j), a
+ * memristor of conductance G_ij at every crossing, and wire resistors between
+ * neighbouring devices.  Source V_i drives word line i at its first column
+ * through R_s; the far end of every word line is open (Eq. 2); the top of every
+ * bit line is open (Eq. 3); the bottom of bit line j is tied to ground through
+ * R_sense, and the current through that termination is output I_j.  Word-line
+ * segments are R_w, bit-line segments R_b.  With R_s = R_w and R_sense = R_b
+ * this is exactly the paper's circuit (its Eq. 5 uses G_WL for the source
+ * segment).  Nodal analysis gives a symmetric 2MN x 2MN system G v = i.
+ *
+ * Method (Sec. II-C, Sec. III-A): decompose the nodal matrix once per
+ * conductance map, then run forward/back substitution for every input vector
+ * of a batch.  libxbar eliminates each bit line's tridiagonal chain inside its
+ * column, which leaves a block-tridiagonal system over the N columns with
+ * dense M x M blocks, and factors that with block Thomas; the substitutions
+ * become chains of dense products streamed over panels of input vectors.
+ *
+ * Conventions
+ *   - Pointers may be host or device memory.  The library asks the CUDA
+ *     runtime which one each pointer is.  Device buffers are used in place;
+ *     host buffers are staged through library-owned device memory with copies
+ *     on the handle's stream, and such calls return only once the stream has
+ *     drained.  With all-device buffers the work is asynchronous on the
+ *     handle's stream; results are valid once the caller synchronises it.
+ *   - Matrices are row-major and dense: G is M x N (G[i*N + j] is the device
+ *     at word line i, bit line j); V is B x M (row b is one input vector, in
+ *     volts); I is B x N (amperes); node voltages are B x M x N.
+ *   - Every call returns an xbar_status; none exits or throws.  On failure
+ *     xbar_last_error() returns a message for the calling thread.
+ *   - Errors detected on the device (a bounded wait that timed out, a
+ *     non-finite value) are recorded in a device status word and reported by
+ *     the next call that synchronises (xbar_solve always does when it
+ *     iterates; xbar_sync does on request).
+ */
+#ifndef XBAR_H
+#define XBAR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xbar_s* xbar_t;
+typedef struct xbar_batch_s* xbar_batch_t;
+
+typedef enum {
+  XBAR_OK = 0,
+  XBAR_EINVAL = 1,    /* invalid argument (size, resistance, conductance, pointer, precision) */
+  XBAR_ENOMEM = 2,    /* device or host allocation failed */
+  XBAR_ECUDA = 3,     /* CUDA runtime error */
+  XBAR_ESTATE = 4,    /* call out of order, e.g. solve before factor */
+  XBAR_ENOTCONV = 5,  /* iterative refinement did not reach tol within max_iter */
+  XBAR_ETIMEOUT = 6   /* a bounded device-side wait expired; the kernel returned early */
+} xbar_status;
+
+typedef enum {
+  /* Plain FP64: factor and substitutions in double precision, no refinement. */
+  XBAR_FP64 = 0,
+  /* Mixed: diagonal equilibration, FP32 factor and FP32 substitutions, then
+   * iterative refinement whose residual r = b - A x and solution update are
+   * computed in FP64. */
+  XBAR_FP32_IR = 1
+} xbar_precision;
+
+typedef struct {
+  int iters;          /* refinement corrections applied (0 for XBAR_FP64) */
+  double max_rel_dI;  /* max over (b, j) of |dI| / |I| of the last correction */
+  double resid_inf;   /* max |r| of the last FP64 residual, in amperes (0 for XBAR_FP64) */
+  double err_est;     /* estimated max relative current error of the result */
+  int n_fallback;     /* unused by the exact solver (0); see the batch API */
+} xbar_solve_info;
+
+/*
+ * xbar_assemble -- build the nodal system of one crossbar (Sec. II-A,
+ * Eqs. 1-7) and create a handle for it.
+ *   M, N          word lines and bit lines, 1 <= M <= 1024, N >= 1.
+ *   G             M x N conductances in siemens, finite and >= 0 (host or
+ *                 device; copied, so the caller may free it on return).
+ *   R_s, R_w, R_b, R_sense   source, word-line segment, bit-line segment and
+ *                 sense resistances in ohms, finite and > 0.
+ *   cuda_stream   cudaStream_t all work of this handle runs on (NULL = legacy
+ *                 default stream).
+ *   out           receives the handle; owns all device memory it allocates.
+ * Errors: XBAR_EINVAL for out-of-range sizes, non-positive or non-finite
+ * resistances, negative or non-finite conductances (checked on the host after
+ * copying G), or NULL pointers; XBAR_ENOMEM; XBAR_ECUDA.
+ */
+xbar_status xbar_assemble(int M, int N, const double* G, double R_s, double R_w, double R_b,
+                          double R_sense, void* cuda_stream, xbar_t* out);
+
+/*
+ * xbar_factor -- decompose the assembled system once (Sec. II-C, LU of the
+ * nodal matrix; Sec. III-A, one decomposition per batch).  Block Thomas over
+ * the N columns: for each column j the M x M Schur complement
+ *   Z_j = C_j - g_w^2 X_{j-1},   X_j = Z_j^{-1},
+ * where C_j is the column's word-line block after its bit-line chain is
+ * eliminated.  Diagonals are formed without subtraction from the grounded
+ * row sums, so the factor keeps high relative accuracy in FP32.
+ * The factor (N x M x M values) is stored in the handle.  Calling it again
+ * re-factors (e.g. with another precision).
+ * Errors: XBAR_EINVAL (bad handle or precision), XBAR_ENOMEM, XBAR_ECUDA,
+ * XBAR_ETIMEOUT (a cross-block wait of the cooperative factor kernel expired).
+ */
+xbar_status xbar_factor(xbar_t h, xbar_precision p);
+
+/*
+ * xbar_solve -- substitute a batch of input vectors (Sec. II-C forward/back
+ * substitution; Sec. III-A batch processing) and extract outputs.
+ *   B          number of input vectors, >= 0 (B = 0 is a no-op).
+ *   V          B x M input voltages (host or device).
+ *   I          B x N bit-line termination currents (output, host or device).
+ *   vWL, vBL   B x M x N word-line / bit-line node voltages (outputs, may be
+ *              NULL; host or device).
+ *   tol        XBAR_FP32_IR only: stop when max |dI|/|I| of a correction is
+ *              <= tol (e.g. 1e-8); ignored for XBAR_FP64.
+ *   max_iter   XBAR_FP32_IR only: most corrections to apply (>= 1).
+ *   info       optional diagnostics (may be NULL).
+ * Errors: XBAR_ESTATE if not factored; XBAR_EINVAL for B < 0, NULL V or I, or
+ * max_iter < 1 in mixed mode; XBAR_ENOTCONV if refinement did not reach tol
+ * (outputs then hold the last iterate); XBAR_ENOMEM; XBAR_ECUDA.
+ */
+xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, double* vWL, double* vBL,
+                       double tol, int max_iter, xbar_solve_info* info);
+
+/*
+ * xbar_set_conductances -- re-assemble the handle for a new conductance map G
+ * (same M, N and resistances; host or device pointer, validated as in
+ * xbar_assemble) without reallocating.  The handle becomes unfactored.
+ * Errors: XBAR_EINVAL (NULL handle/G, negative or non-finite G), XBAR_ECUDA.
+ */
+xbar_status xbar_set_conductances(xbar_t h, const double* G);
+
+/* Per-phase device time of one handle, from CUDA events recorded on its stream
+ * around every kernel launch while profiling is enabled. */
+typedef enum {
+  XBAR_PHASE_ASSEMBLE = 0,  /* nodal assembly kernels */
+  XBAR_PHASE_FACTOR = 1,    /* block Thomas factor kernel */
+  XBAR_PHASE_SWEEP = 2,     /* forward/back substitution + current extraction */
+  XBAR_PHASE_RESID = 3,     /* FP64 residual of refinement */
+  XBAR_PHASE_UPDATE = 4,    /* FP64 solution update of refinement */
+  XBAR_PHASE_OUTPUT = 5,    /* node-voltage extraction and layout */
+  XBAR_NPHASES = 6
+} xbar_phase;
+
+typedef struct {
+  int launches[XBAR_NPHASES];   /* kernel launches per phase */
+  double ms[XBAR_NPHASES];      /* summed device milliseconds per phase */
+} xbar_profile;
+
+/* Enable (1) or disable (0) event timing on the handle; enabling resets it. */
+xbar_status xbar_profile_enable(xbar_t h, int enable);
+/* Synchronise the stream and return the accumulated per-phase times
+ * (out may not be NULL); reset != 0 clears the accumulators afterwards. */
+xbar_status xbar_profile_read(xbar_t h, xbar_profile* out, int reset);
+
+/* Wait for the handle's stream and report any device-recorded error. */
+xbar_status xbar_sync(xbar_t h);
+
+/* Release the handle and all memory it owns.  NULL is accepted. */
+xbar_status xbar_destroy(xbar_t h);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* xbar_last_error(void);
+
+/* Library version string. */
+const char* xbar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XBAR_H */

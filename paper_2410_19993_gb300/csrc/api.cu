@@ -1,0 +1,599 @@
+// api.cu -- host implementation of the libxbar C ABI (include/xbar.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/xbar.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace xbar;
+
+static thread_local std::string g_last_error;
+
+static xbar_status fail(xbar_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define XB_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      if (e_ == cudaErrorMemoryAllocation) {                                               \
+        cudaGetLastError();                                                                \
+        return fail(XBAR_ENOMEM, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      }                                                                                    \
+      return fail(XBAR_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                      \
+  } while (0)
+
+namespace {
+
+// device allocation owned by a handle; freed in reverse order on destroy
+struct DevArena {
+  std::vector<void*> ptrs;
+  cudaError_t alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  void release(void* p) {
+    for (size_t k = 0; k < ptrs.size(); ++k)
+      if (ptrs[k] == p) {
+        cudaFree(p);
+        ptrs.erase(ptrs.begin() + k);
+        return;
+      }
+  }
+  void free_all() {
+    for (size_t k = ptrs.size(); k-- > 0;) cudaFree(ptrs[k]);
+    ptrs.clear();
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// growable device buffer
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+cudaError_t ensure(DevArena& A, Buf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  if (b.p) A.release(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = A.alloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+int round_up(int a, int m) { return ((a + m - 1) / m) * m; }
+
+}  // namespace
+
+struct xbar_s {
+  MapDev m;
+  double R[4] = {0, 0, 0, 0};
+  cudaStream_t st = nullptr;
+  int dev = 0, nsm = 0;
+  int factored = 0;
+  xbar_precision prec = XBAR_FP64;
+  DevArena A;
+  unsigned* status = nullptr;
+  // factor
+  Buf X, fsig, fpbuf, fbar, fparams;
+  // solve workspace
+  Buf z, dhat, rhat, w64, phi, maxrel, rmax;
+  // staging for host pointers
+  Buf sV, sI, svWL, svBL;
+  // profiling: events recorded around launches, resolved in xbar_profile_read
+  int prof_on = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  xbar_profile prof;
+};
+
+// RAII scope that brackets the launches of one phase with events when profiling is on
+struct PhaseScope {
+  xbar_s* h;
+  int phase;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int nlaunch;
+  PhaseScope(xbar_s* h_, int ph, int n = 1) : h(h_), phase(ph), nlaunch(n) {
+    if (!h->prof_on) return;
+    e0 = take();
+    e1 = take();
+    if (e0) cudaEventRecord(e0, h->st);
+  }
+  cudaEvent_t take() {
+    if (!h->ev_pool.empty()) {
+      cudaEvent_t e = h->ev_pool.back();
+      h->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  ~PhaseScope() {
+    if (!h->prof_on || !e0 || !e1) return;
+    cudaEventRecord(e1, h->st);
+    h->pending.push_back({phase, {e0, e1}});
+    h->prof.launches[phase] += nlaunch;
+  }
+};
+
+static const char* kVersion = "libxbar 0.1 (sm_103a)";
+
+extern "C" const char* xbar_version(void) { return kVersion; }
+extern "C" const char* xbar_last_error(void) { return g_last_error.c_str(); }
+
+static xbar_status check_status(xbar_t h) {
+  unsigned s = 0;
+  XB_CUDA(cudaMemcpyAsync(&s, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  XB_CUDA(cudaStreamSynchronize(h->st));
+  if (s) {
+    XB_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+    if (s & XBAR_DEV_TIMEOUT) return fail(XBAR_ETIMEOUT, "a bounded device wait expired (status 0x%x)", s);
+    if (s & XBAR_DEV_BADLAUNCH) return fail(XBAR_ECUDA, "kernel launch shape inconsistent (status 0x%x)", s);
+    if (s & XBAR_DEV_NONFINITE) return fail(XBAR_ECUDA, "non-finite value produced (status 0x%x)", s);
+  }
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, double R_w, double R_b,
+                                     double R_sense, void* cuda_stream, xbar_t* out) {
+  if (!out) return fail(XBAR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (M < 1 || M > 1024) return fail(XBAR_EINVAL, "M=%d outside [1, 1024]", M);
+  if (N < 1 || N > (1 << 20)) return fail(XBAR_EINVAL, "N=%d outside [1, 2^20]", N);
+  if (!G) return fail(XBAR_EINVAL, "G is NULL");
+  const double R[4] = {R_s, R_w, R_b, R_sense};
+  const char* names[4] = {"R_s", "R_w", "R_b", "R_sense"};
+  for (int k = 0; k < 4; ++k)
+    if (!(R[k] > 0.0) || !isfinite(R[k])) return fail(XBAR_EINVAL, "%s=%g must be finite and > 0", names[k], R[k]);
+
+  // validate G on the host
+  std::vector<double> Gh((size_t)M * N);
+  const bool gdev = is_device_ptr(G);
+  if (gdev) {
+    cudaError_t e = cudaMemcpy(Gh.data(), G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(XBAR_ECUDA, "copy of G: %s", cudaGetErrorString(e));
+  } else {
+    memcpy(Gh.data(), G, Gh.size() * sizeof(double));
+  }
+  for (size_t k = 0; k < Gh.size(); ++k)
+    if (!(Gh[k] >= 0.0) || !isfinite(Gh[k]))
+      return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, Gh[k]);
+
+  xbar_s* h = new xbar_s();
+  h->st = (cudaStream_t)cuda_stream;
+  for (int k = 0; k < 4; ++k) h->R[k] = R[k];
+  cudaGetDevice(&h->dev);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
+  MapDev& m = h->m;
+  m.M = M;
+  m.N = N;
+  m.Mp = round_up(M, 16);
+  m.gs = 1.0 / R_s;
+  m.gw = 1.0 / R_w;
+  m.gb = 1.0 / R_b;
+  m.go = 1.0 / R_sense;
+  const size_t nv = (size_t)N * m.Mp;
+  auto cleanup = [&](xbar_status s) {
+    h->A.free_all();
+    delete h;
+    return s;
+  };
+#define XB_ALLOC(ptr, bytes)                                                          \
+  do {                                                                                \
+    cudaError_t e_ = h->A.alloc((void**)&(ptr), (bytes));                             \
+    if (e_ != cudaSuccess) {                                                          \
+      cudaGetLastError();                                                             \
+      return cleanup(fail(XBAR_ENOMEM, "cudaMalloc(%zu): %s", (size_t)(bytes), cudaGetErrorString(e_))); \
+    }                                                                                 \
+  } while (0)
+  XB_ALLOC(m.Gc, nv * 8);
+  XB_ALLOC(m.dW, nv * 8);
+  XB_ALLOC(m.h, nv * 8);
+  XB_ALLOC(m.tha, nv * 8);
+  XB_ALLOC(m.thc, nv * 8);
+  XB_ALLOC(m.tdiag, nv * 8);
+  XB_ALLOC(m.rho, nv * 8);
+  XB_ALLOC(m.s_eq, nv * 8);
+  XB_ALLOC(m.e_eq, nv * 8);
+  XB_ALLOC(m.e_pl, nv * 8);
+  XB_ALLOC(m.hs_eq, nv * 8);
+  XB_ALLOC(m.src_eq, (size_t)m.Mp * 8);
+  XB_ALLOC(m.src_pl, (size_t)m.Mp * 8);
+  XB_ALLOC(m.s32, nv * 4);
+  XB_ALLOC(m.e32, nv * 4);
+  XB_ALLOC(m.hs32, nv * 4);
+  XB_ALLOC(m.src32, (size_t)m.Mp * 4);
+  XB_ALLOC(m.Coff, nv * m.Mp * 8);
+  XB_ALLOC(h->status, sizeof(unsigned));
+  double* Gd = nullptr;
+  XB_ALLOC(Gd, (size_t)M * N * 8);
+#undef XB_ALLOC
+  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Gd, Gh.data(), (size_t)M * N * 8, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) {
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
+    e = launch_assemble(m, Gd, h->st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cleanup(fail(XBAR_ECUDA, "assembly: %s", cudaGetErrorString(e)));
+  h->A.release(Gd);
+  *out = h;
+  return XBAR_OK;
+}
+
+template <typename T>
+static xbar_status do_factor(xbar_t h, bool equilibrate) {
+  MapDev& m = h->m;
+  const int Mp = m.Mp, N = m.N;
+  const int PB = factor_panel_width<T>();
+  int bpm;
+  if (Mp <= 32) bpm = 1;
+  else bpm = std::min(h->nsm, Mp / (sizeof(T) == 8 ? 2 : 4));
+  if (bpm < 1) bpm = 1;
+  XB_CUDA(ensure(h->A, h->X, (size_t)N * Mp * Mp * sizeof(T)));
+  XB_CUDA(ensure(h->A, h->fsig, 2 * (size_t)Mp * sizeof(T)));
+  XB_CUDA(ensure(h->A, h->fpbuf, 2 * (size_t)PB * Mp * sizeof(T)));
+  XB_CUDA(ensure(h->A, h->fbar, 2 * sizeof(unsigned)));
+  XB_CUDA(ensure(h->A, h->fparams, sizeof(FactorParams<T>)));
+  FactorParams<T> fp;
+  fp.M = m.M;
+  fp.Mp = Mp;
+  fp.N = N;
+  fp.gsrc = m.gs;
+  fp.gw = m.gw;
+  fp.Coff = m.Coff;
+  fp.h = m.h;
+  fp.s = equilibrate ? m.s_eq : nullptr;
+  fp.e = equilibrate ? m.e_eq : m.e_pl;
+  fp.X = (T*)h->X.p;
+  fp.sig = (T*)h->fsig.p;
+  fp.pbuf = (T*)h->fpbuf.p;
+  fp.bar = (unsigned*)h->fbar.p;
+  XB_CUDA(cudaMemsetAsync(h->fbar.p, 0, 2 * sizeof(unsigned), h->st));
+  XB_CUDA(cudaMemcpyAsync(h->fparams.p, &fp, sizeof(fp), cudaMemcpyHostToDevice, h->st));
+  PhaseScope ps(h, XBAR_PHASE_FACTOR);
+  XB_CUDA(launch_factor<T>((const FactorParams<T>*)h->fparams.p, 1, Mp, bpm, h->status, h->st));
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_factor(xbar_t h, xbar_precision p) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (p != XBAR_FP64 && p != XBAR_FP32_IR) return fail(XBAR_EINVAL, "unknown precision %d", (int)p);
+  XB_CUDA(cudaSetDevice(h->dev));
+  h->factored = 0;
+  xbar_status s = (p == XBAR_FP64) ? do_factor<double>(h, false) : do_factor<float>(h, true);
+  if (s != XBAR_OK) return s;
+  h->prec = p;
+  h->factored = 1;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_sync(xbar_t h) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  XB_CUDA(cudaSetDevice(h->dev));
+  XB_CUDA(cudaStreamSynchronize(h->st));
+  return check_status(h);
+}
+
+extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, double* vWL, double* vBL,
+                                  double tol, int max_iter, xbar_solve_info* info) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (info) memset(info, 0, sizeof(*info));
+  if (!h->factored) return fail(XBAR_ESTATE, "xbar_solve called before xbar_factor");
+  if (B < 0) return fail(XBAR_EINVAL, "B=%d < 0", B);
+  if (B == 0) return XBAR_OK;
+  if (!V || !I) return fail(XBAR_EINVAL, "V and I must not be NULL");
+  const bool mixed = h->prec == XBAR_FP32_IR;
+  if (mixed && max_iter < 1) return fail(XBAR_EINVAL, "max_iter=%d < 1", max_iter);
+  if (mixed && !(tol >= 0.0)) return fail(XBAR_EINVAL, "tol=%g must be >= 0", tol);
+  XB_CUDA(cudaSetDevice(h->dev));
+  MapDev& m = h->m;
+  const int M = m.M, Mp = m.Mp, N = m.N;
+  cudaStream_t st = h->st;
+
+  // stage host pointers
+  const bool vdev = is_device_ptr(V), idev = is_device_ptr(I);
+  const bool want_v = vWL || vBL;
+  const bool wdev = !vWL || is_device_ptr(vWL), bdev = !vBL || is_device_ptr(vBL);
+  const double* dV = V;
+  double* dI = I;
+  double *dvWL = vWL, *dvBL = vBL;
+  const size_t nVB = (size_t)B * M, nIB = (size_t)B * N, nvolt = (size_t)B * M * N;
+  if (!vdev) {
+    XB_CUDA(ensure(h->A, h->sV, nVB * 8));
+    XB_CUDA(cudaMemcpyAsync(h->sV.p, V, nVB * 8, cudaMemcpyHostToDevice, st));
+    dV = (const double*)h->sV.p;
+  }
+  if (!idev) {
+    XB_CUDA(ensure(h->A, h->sI, nIB * 8));
+    dI = (double*)h->sI.p;
+  }
+  if (vWL && !wdev) {
+    XB_CUDA(ensure(h->A, h->svWL, nvolt * 8));
+    dvWL = (double*)h->svWL.p;
+  }
+  if (vBL && !bdev) {
+    XB_CUDA(ensure(h->A, h->svBL, nvolt * 8));
+    dvBL = (double*)h->svBL.p;
+  }
+
+  const int Bp = mixed ? sweep_panel_width<float>(Mp, B, h->nsm) : sweep_panel_width<double>(Mp, B, h->nsm);
+  const int nblk = (B + Bp - 1) / Bp;
+  const int Bpad = nblk * Bp;
+  const size_t nst = (size_t)N * Mp * Bpad;
+
+  ResidParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.M = M;
+  rp.Mp = Mp;
+  rp.N = N;
+  rp.B = B;
+  rp.Bpad = Bpad;
+  rp.gs = m.gs;
+  rp.gw = m.gw;
+  rp.Gc = m.Gc;
+  rp.dW = m.dW;
+  rp.h = m.h;
+  rp.tha = m.tha;
+  rp.thc = m.thc;
+  rp.s32 = m.s32;
+  rp.V = dV;
+  rp.I = dI;
+  rp.status = h->status;
+
+  int iters = 0;
+  double last = 0.0, prev = 0.0, rinf = 0.0;
+  bool converged = true;
+  if (!mixed) {
+    XB_CUDA(ensure(h->A, h->z, nst * 8));
+    if (want_v) {
+      XB_CUDA(ensure(h->A, h->w64, nst * 8));
+      XB_CUDA(ensure(h->A, h->phi, nst * 8));
+    }
+    SweepParams<double> sp;
+    sp.M = M;
+    sp.Mp = Mp;
+    sp.N = N;
+    sp.B = B;
+    sp.Bp = Bp;
+    sp.Bpad = Bpad;
+    sp.X = (const double*)h->X.p;
+    sp.e = m.e_pl;
+    sp.hs = m.h;
+    sp.src = m.src_pl;
+    sp.V = dV;
+    sp.rhs = nullptr;
+    sp.z = (double*)h->z.p;
+    sp.w = want_v ? (double*)h->w64.p : nullptr;
+    sp.I = dI;
+    sp.accumulate = 0;
+    sp.max_rel = nullptr;
+    sp.status = h->status;
+    {
+      PhaseScope ps(h, XBAR_PHASE_SWEEP);
+      XB_CUDA(launch_sweep<double>(sp, st));
+    }
+    rp.w = (double*)h->w64.p;
+    rp.phi = (double*)h->phi.p;
+  } else {
+    XB_CUDA(ensure(h->A, h->z, nst * 4));
+    XB_CUDA(ensure(h->A, h->dhat, nst * 4));
+    XB_CUDA(ensure(h->A, h->rhat, nst * 4));
+    XB_CUDA(ensure(h->A, h->w64, nst * 8));
+    XB_CUDA(ensure(h->A, h->phi, nst * 8));
+    XB_CUDA(ensure(h->A, h->maxrel, 16));
+    XB_CUDA(ensure(h->A, h->rmax, 16));
+    rp.w = (double*)h->w64.p;
+    rp.dhat = (const float*)h->dhat.p;
+    rp.phi = (double*)h->phi.p;
+    rp.rhat = (float*)h->rhat.p;
+    rp.rmax = (unsigned long long*)h->rmax.p;
+    SweepParams<float> sp;
+    sp.M = M;
+    sp.Mp = Mp;
+    sp.N = N;
+    sp.B = B;
+    sp.Bp = Bp;
+    sp.Bpad = Bpad;
+    sp.X = (const float*)h->X.p;
+    sp.e = m.e32;
+    sp.hs = m.hs32;
+    sp.src = m.src32;
+    sp.V = dV;
+    sp.rhs = nullptr;
+    sp.z = (float*)h->z.p;
+    sp.w = (float*)h->dhat.p;
+    sp.I = dI;
+    sp.accumulate = 0;
+    sp.max_rel = nullptr;
+    sp.status = h->status;
+    {
+      PhaseScope ps(h, XBAR_PHASE_SWEEP);
+      XB_CUDA(launch_sweep<float>(sp, st));     // x0 = solve32(b)
+    }
+    {
+      PhaseScope ps(h, XBAR_PHASE_UPDATE);
+      XB_CUDA(launch_update(rp, 1, st));        // w = s o dhat, I = h . w
+    }
+    converged = false;
+    bool w_current = true;                      // w includes every correction so far
+    float mr = 0.0f;
+    for (int it = 0; it < max_iter; ++it) {
+      XB_CUDA(cudaMemsetAsync(h->rmax.p, 0, 8, st));
+      {
+        PhaseScope ps(h, XBAR_PHASE_RESID);
+        XB_CUDA(launch_resid(rp, st));          // rhat = s o (b - A w)   [FP64]
+      }
+      XB_CUDA(cudaMemsetAsync(h->maxrel.p, 0, 4, st));
+      sp.V = nullptr;
+      sp.rhs = (const float*)h->rhat.p;
+      sp.accumulate = 1;
+      sp.max_rel = (float*)h->maxrel.p;
+      {
+        PhaseScope ps(h, XBAR_PHASE_SWEEP);
+        XB_CUDA(launch_sweep<float>(sp, st));   // dhat = solve32(rhat), I += dI
+      }
+      w_current = false;
+      ++iters;
+      unsigned long long rbits = 0;
+      XB_CUDA(cudaMemcpyAsync(&mr, h->maxrel.p, 4, cudaMemcpyDeviceToHost, st));
+      XB_CUDA(cudaMemcpyAsync(&rbits, h->rmax.p, 8, cudaMemcpyDeviceToHost, st));
+      XB_CUDA(cudaStreamSynchronize(st));
+      memcpy(&rinf, &rbits, 8);
+      prev = last;
+      last = mr;
+      if (!(mr == mr)) break;                   // NaN: give up, reported below
+      if (mr <= tol) {
+        converged = true;
+        break;
+      }
+      {
+        PhaseScope ps(h, XBAR_PHASE_UPDATE);
+        XB_CUDA(launch_update(rp, 0, st));      // w += s o dhat, I = h . w   [FP64]
+      }
+      w_current = true;
+    }
+    if (want_v && !w_current) {
+      PhaseScope ps(h, XBAR_PHASE_UPDATE);
+      XB_CUDA(launch_update(rp, 0, st));
+    }
+  }
+  if (want_v) {
+    PhaseScope ps(h, XBAR_PHASE_OUTPUT, 1 + (dvWL ? 1 : 0) + (dvBL ? 1 : 0));
+    XB_CUDA(launch_blvolt(rp, (double*)h->phi.p, st));
+    if (dvWL) XB_CUDA(launch_to_user_layout((const double*)h->w64.p, dvWL, M, Mp, N, B, Bpad, st));
+    if (dvBL) XB_CUDA(launch_to_user_layout((const double*)h->phi.p, dvBL, M, Mp, N, B, Bpad, st));
+  }
+  const bool any_host = !idev || (vWL && !wdev) || (vBL && !bdev) || !vdev;
+  if (!idev) XB_CUDA(cudaMemcpyAsync(I, dI, nIB * 8, cudaMemcpyDeviceToHost, st));
+  if (vWL && !wdev) XB_CUDA(cudaMemcpyAsync(vWL, dvWL, nvolt * 8, cudaMemcpyDeviceToHost, st));
+  if (vBL && !bdev) XB_CUDA(cudaMemcpyAsync(vBL, dvBL, nvolt * 8, cudaMemcpyDeviceToHost, st));
+  if (mixed || any_host) {
+    xbar_status s = check_status(h);
+    if (s != XBAR_OK) return s;
+  }
+  if (info) {
+    info->iters = iters;
+    info->max_rel_dI = last;
+    info->resid_inf = rinf;
+    double est = last;
+    if (iters >= 2 && prev > 0.0) {
+      const double rate = last / prev;
+      if (rate < 1.0) est = last * rate / (1.0 - rate);
+    }
+    info->err_est = mixed ? est : 0.0;
+    info->n_fallback = 0;
+  }
+  if (mixed && !converged)
+    return fail(XBAR_ENOTCONV, "refinement stopped after %d corrections with max |dI|/|I| = %g > tol = %g",
+                iters, last, tol);
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_destroy(xbar_t h) {
+  if (!h) return XBAR_OK;
+  cudaSetDevice(h->dev);
+  cudaStreamSynchronize(h->st);
+  for (auto& pe : h->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->A.free_all();
+  delete h;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_profile_enable(xbar_t h, int enable) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  XB_CUDA(cudaSetDevice(h->dev));
+  XB_CUDA(cudaStreamSynchronize(h->st));
+  for (auto& pe : h->pending) {
+    h->ev_pool.push_back(pe.second.first);
+    h->ev_pool.push_back(pe.second.second);
+  }
+  h->pending.clear();
+  memset(&h->prof, 0, sizeof(h->prof));
+  h->prof_on = enable ? 1 : 0;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_profile_read(xbar_t h, xbar_profile* out, int reset) {
+  if (!h || !out) return fail(XBAR_EINVAL, "handle or out is NULL");
+  XB_CUDA(cudaSetDevice(h->dev));
+  XB_CUDA(cudaStreamSynchronize(h->st));
+  for (auto& pe : h->pending) {
+    float ms = 0.0f;
+    XB_CUDA(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+    h->prof.ms[pe.first] += ms;
+    h->ev_pool.push_back(pe.second.first);
+    h->ev_pool.push_back(pe.second.second);
+  }
+  h->pending.clear();
+  *out = h->prof;
+  if (reset) memset(&h->prof, 0, sizeof(h->prof));
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
+  if (!h || !G) return fail(XBAR_EINVAL, "handle or G is NULL");
+  XB_CUDA(cudaSetDevice(h->dev));
+  MapDev& m = h->m;
+  const size_t n = (size_t)m.M * m.N;
+  const bool gdev = is_device_ptr(G);
+  // validation needs the values on the host
+  std::vector<double> Gh(n);
+  if (gdev) {
+    XB_CUDA(cudaMemcpyAsync(Gh.data(), G, n * 8, cudaMemcpyDeviceToHost, h->st));
+    XB_CUDA(cudaStreamSynchronize(h->st));
+  } else {
+    memcpy(Gh.data(), G, n * 8);
+  }
+  for (size_t k = 0; k < n; ++k)
+    if (!(Gh[k] >= 0.0) || !isfinite(Gh[k])) return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, Gh[k]);
+  XB_CUDA(ensure(h->A, h->sV, std::max(h->sV.bytes, n * 8)));
+  const double* Gd = G;
+  if (!gdev) {
+    XB_CUDA(cudaMemcpyAsync(h->sV.p, Gh.data(), n * 8, cudaMemcpyHostToDevice, h->st));
+    Gd = (const double*)h->sV.p;
+  }
+  h->factored = 0;
+  {
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
+    XB_CUDA(launch_assemble(m, Gd, h->st));
+  }
+  if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
+  return XBAR_OK;
+}

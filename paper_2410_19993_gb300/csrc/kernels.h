@@ -1,0 +1,119 @@
+// kernels.h -- host-side declarations of the libxbar kernel launchers.
+//
+// Layouts (all device memory, row-major):
+//   per-column vectors   [N][Mp]        element (j, i) at j*Mp + i (Mp = M padded to 16)
+//   per-column matrices  [N][Mp][Mp]    block j, row i, column k at (j*Mp + i)*Mp + k
+//   batch vectors        [N][Mp][Bpad]  column j, row i, input vector b at (j*Mp + i)*Bpad + b
+//   user inputs          V[B][M], I[B][N], node voltages [B][M][N]
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace xbar {
+
+// Per-crossbar assembled data (device pointers, FP64 unless noted).
+struct MapDev {
+  int M = 0, N = 0, Mp = 0;
+  double gs = 0, gw = 0, gb = 0, go = 0;
+  double* Gc = nullptr;     // [N][Mp]  G transposed: Gc[j][i] = G[i][j]
+  double* dW = nullptr;     // [N][Mp]  word-line row diagonal of the nodal matrix
+  double* h = nullptr;      // [N][Mp]  I_j = h_j . w_j  (w_j = word-line voltages of column j)
+  double* tha = nullptr;    // [N][Mp]  bit-line chain forward sweep: phi_i = tha_i w_i + thc_i phi_{i-1}
+  double* thc = nullptr;    // [N][Mp]  and back sweep u_i = phi_i + thc_i u_{i+1}
+  double* tdiag = nullptr;  // [N][Mp]  diagonal of the inverse bit-line chain matrix
+  double* rho = nullptr;    // [N][Mp]  ratio of consecutive inverse entries along a row
+  double* Coff = nullptr;   // [N][Mp][Mp] off-diagonal of the column block after bit-line elimination
+  double* s_eq = nullptr;   // [N][Mp]  diagonal equilibration scale (dW^-1/2)
+  double* e_eq = nullptr;   // [N][Mp]  coupling of column j to j+1, equilibrated
+  double* e_pl = nullptr;   // [N][Mp]  coupling, plain (g_w)
+  double* hs_eq = nullptr;  // [N][Mp]  s_eq * h
+  double* src_eq = nullptr; // [Mp]     g_s * s_eq[0]
+  double* src_pl = nullptr; // [Mp]     g_s
+  float* s32 = nullptr;     // FP32 copies of the equilibrated vectors
+  float* e32 = nullptr;
+  float* hs32 = nullptr;
+  float* src32 = nullptr;
+};
+
+// ---- assembly ---------------------------------------------------------------------------------
+cudaError_t launch_assemble(const MapDev& m, const double* G_dev, cudaStream_t st);
+
+// ---- factor -----------------------------------------------------------------------------------
+template <typename T>
+struct FactorParams {
+  int M, Mp, N;
+  double gsrc, gw;
+  const double* Coff;
+  const double* h;
+  const double* s;    // nullptr = no equilibration
+  const double* e;
+  T* X;               // [N][Mp][Mp] output
+  T* sig;             // [2][Mp] scratch
+  T* pbuf;            // [2][PB][Mp] scratch
+  unsigned* bar;      // 2 words, zeroed
+};
+
+// One group of `blocks_per_map` co-resident blocks factors each map; `maps` is a device array.
+template <typename T>
+cudaError_t launch_factor(const FactorParams<T>* maps_dev, int nmaps, int Mp_max, int blocks_per_map,
+                          unsigned* status, cudaStream_t st);
+template <typename T>
+int factor_panel_width();
+template <typename T>
+size_t factor_smem_bytes(int Mp, int rows_per_block);
+
+// ---- sweeps (forward + back substitution, current extraction) ---------------------------------
+template <typename T>
+struct SweepParams {
+  int M, Mp, N, B, Bp, Bpad;
+  const T* X;          // [N][Mp][Mp]
+  const T* e;          // [N][Mp]
+  const T* hs;         // [N][Mp]
+  const T* src;        // [Mp]   initial mode: rhs_0 = src * V_b
+  const double* V;     // [B][M] initial mode, else nullptr
+  const T* rhs;        // [N][Mp][Bpad] correction mode, else nullptr
+  T* z;                // [N][Mp][Bpad] scratch
+  T* w;                // [N][Mp][Bpad] solution, or nullptr
+  double* I;           // [B][N]
+  int accumulate;      // 0: I = dI   1: I += dI
+  float* max_rel;      // atomic max of |dI| / |I| (accumulate mode), or nullptr
+  unsigned* status;
+};
+
+template <typename T>
+cudaError_t launch_sweep(const SweepParams<T>& p, cudaStream_t st);
+template <typename T>
+int sweep_panel_width(int Mp, int B, int nsm);
+
+// ---- FP64 refinement kernels and node voltages ------------------------------------------------
+struct ResidParams {
+  int M, Mp, N, B, Bpad;
+  double gs, gw;
+  const double* Gc;
+  const double* dW;
+  const double* h;
+  const double* tha;
+  const double* thc;
+  const float* s32;
+  const double* V;      // [B][M]
+  double* w;            // [N][Mp][Bpad] FP64 word-line voltages (state)
+  const float* dhat;    // [N][Mp][Bpad] scaled correction from the FP32 sweep
+  double* phi;          // [N][Mp][Bpad] scratch
+  float* rhat;          // [N][Mp][Bpad] scaled residual for the next FP32 sweep
+  double* I;            // [B][N]
+  unsigned long long* rmax;  // bit pattern of max |r| (non-negative double)
+  unsigned* status;
+};
+// w = (first ? 0 : w) + s * dhat ; I = h . w
+cudaError_t launch_update(const ResidParams& p, int first, cudaStream_t st);
+// rhat = s * (b - K w)   with K the word-line system after bit-line elimination
+cudaError_t launch_resid(const ResidParams& p, cudaStream_t st);
+// bit-line voltages u = T^-1 (G o w) into `u` ([N][Mp][Bpad]), in place of phi
+cudaError_t launch_blvolt(const ResidParams& p, double* u, cudaStream_t st);
+// out[b][i][j] = src[(j*Mp + i)*Bpad + b]
+cudaError_t launch_to_user_layout(const double* src, double* out, int M, int Mp, int N, int B, int Bpad,
+                                  cudaStream_t st);
+// FP64 -> FP32 copy
+cudaError_t launch_d2f(const double* a, float* b, size_t n, cudaStream_t st);
+
+}  // namespace xbar

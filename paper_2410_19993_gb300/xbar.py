@@ -1,0 +1,176 @@
+"""ctypes binding of libxbar (C ABI in include/xbar.h): argument marshalling only.
+
+Every step of the solve runs in libxbar.so's CUDA kernels.  Arrays may be
+torch tensors (CUDA or CPU, float64, contiguous) or numpy float64 arrays; the
+library itself decides whether each pointer is host or device memory.  If the
+library cannot be loaded every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+XBAR_OK, XBAR_EINVAL, XBAR_ENOMEM, XBAR_ECUDA, XBAR_ESTATE, XBAR_ENOTCONV, XBAR_ETIMEOUT = range(7)
+XBAR_FP64, XBAR_FP32_IR = 0, 1
+STATUS_NAMES = {0: "XBAR_OK", 1: "XBAR_EINVAL", 2: "XBAR_ENOMEM", 3: "XBAR_ECUDA", 4: "XBAR_ESTATE",
+                5: "XBAR_ENOTCONV", 6: "XBAR_ETIMEOUT"}
+PRECISIONS = {"fp64": XBAR_FP64, "fp32_ir": XBAR_FP32_IR}
+
+
+class XbarError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("max_rel_dI", ctypes.c_double), ("resid_inf", ctypes.c_double),
+                ("err_est", ctypes.c_double), ("n_fallback", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PHASES = ["assemble", "factor", "sweep", "resid", "update", "output"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int * 6), ("ms", ctypes.c_double * 6)]
+
+    def as_dict(self):
+        return {ph: {"launches": int(self.launches[k]), "ms": float(self.ms[k])} for k, ph in enumerate(PHASES)}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libxbar.so (building it first if needed); raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build._stale()):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libxbar.so not found at {path}; run paper_2410_19993_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.xbar_assemble.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, _vp, ctypes.POINTER(_vp)]
+    lib.xbar_factor.argtypes = [_vp, ctypes.c_int]
+    lib.xbar_solve.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                               ctypes.POINTER(SolveInfo)]
+    lib.xbar_sync.argtypes = [_vp]
+    lib.xbar_set_conductances.argtypes = [_vp, _vp]
+    lib.xbar_profile_enable.argtypes = [_vp, ctypes.c_int]
+    lib.xbar_profile_read.argtypes = [_vp, ctypes.POINTER(Profile), ctypes.c_int]
+    lib.xbar_destroy.argtypes = [_vp]
+    lib.xbar_last_error.restype = ctypes.c_char_p
+    lib.xbar_version.restype = ctypes.c_char_p
+    for f in ("xbar_assemble", "xbar_factor", "xbar_solve", "xbar_sync", "xbar_destroy", "xbar_set_conductances",
+              "xbar_profile_enable", "xbar_profile_read"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().xbar_last_error().decode()
+
+
+def _check(status):
+    if status != XBAR_OK:
+        raise XbarError(status, last_error())
+
+
+def _ptr(a, dtype=np.float64):
+    """Data pointer of a contiguous float64 torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a contiguous float64 numpy array")
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+@dataclass
+class Crossbar:
+    """Handle of one assembled crossbar (xbar_assemble); factor() then solve() any number of batches."""
+    M: int
+    N: int
+    handle: int
+
+    @classmethod
+    def assemble(cls, G, Rs, Rw, Rb, Rsense, stream=None):
+        lib = load()
+        M, N = int(G.shape[0]), int(G.shape[1])
+        h = _vp()
+        _check(lib.xbar_assemble(M, N, _ptr(G), Rs, Rw, Rb, Rsense, _stream_ptr(stream), ctypes.byref(h)))
+        return cls(M, N, h.value)
+
+    def factor(self, precision="fp64"):
+        _check(load().xbar_factor(self.handle, PRECISIONS.get(precision, precision)))
+        return self
+
+    def solve(self, V, I, vWL=None, vBL=None, tol=1e-8, max_iter=10, raise_on_error=True):
+        """xbar_solve: V [B x M] -> I [B x N] (+ node voltages [B x M x N]); returns (status, info dict)."""
+        info = SolveInfo()
+        B = int(V.shape[0])
+        st = load().xbar_solve(self.handle, B, _ptr(V), _ptr(I), _ptr(vWL), _ptr(vBL), tol, max_iter,
+                               ctypes.byref(info))
+        if raise_on_error:
+            _check(st)
+        return st, info.as_dict()
+
+    def set_conductances(self, G):
+        _check(load().xbar_set_conductances(self.handle, _ptr(G)))
+        return self
+
+    def profile_enable(self, on=True):
+        _check(load().xbar_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        pr = Profile()
+        _check(load().xbar_profile_read(self.handle, ctypes.byref(pr), 1 if reset else 0))
+        return pr.as_dict()
+
+    def sync(self):
+        _check(load().xbar_sync(self.handle))
+
+    def destroy(self):
+        if self.handle:
+            load().xbar_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def exported_symbols():
+    """Names declared in include/xbar.h (every one must be exported by libxbar.so)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(_build.HERE), "include", "xbar.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:xbar_status|const char\*)\s+(xbar_\w+)\s*\(", hdr, re.M)))

@@ -1,0 +1,48 @@
+"""libxbar.so builds, loads and exports every entry point declared in include/xbar.h (no GPU needed)."""
+import ctypes
+import subprocess
+
+from paper_2410_19993_gb300 import build, xbar
+
+
+def test_header_declares_the_boundary():
+    names = xbar.exported_symbols()
+    for n in ["xbar_assemble", "xbar_factor", "xbar_solve", "xbar_destroy", "xbar_last_error", "xbar_sync",
+              "xbar_version"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for n in xbar.exported_symbols():
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    for n in xbar.exported_symbols():
+        assert f" T {n}" in out, n
+
+
+def test_version_and_error_string_without_gpu():
+    lib = xbar.load()
+    assert lib.xbar_version().startswith(b"libxbar")
+    assert isinstance(lib.xbar_last_error(), bytes)
+
+
+def test_host_side_argument_checks_without_gpu():
+    """Argument validation happens on the host before any CUDA call."""
+    import numpy as np
+    lib = xbar.load()
+    h = ctypes.c_void_p()
+    G = np.ones((4, 4))
+    assert lib.xbar_assemble(0, 4, G.ctypes.data, 1, 1, 1, 1, None, ctypes.byref(h)) == xbar.XBAR_EINVAL
+    assert lib.xbar_assemble(4, 4, G.ctypes.data, 1, -1, 1, 1, None, ctypes.byref(h)) == xbar.XBAR_EINVAL
+    assert lib.xbar_assemble(4, 4, G.ctypes.data, 1, 1, 0.0, 1, None, ctypes.byref(h)) == xbar.XBAR_EINVAL
+    assert lib.xbar_assemble(4, 4, G.ctypes.data, 1, 1, 1, float("nan"), None, ctypes.byref(h)) == xbar.XBAR_EINVAL
+    assert lib.xbar_assemble(4, 4, None, 1, 1, 1, 1, None, ctypes.byref(h)) == xbar.XBAR_EINVAL
+    Gbad = G.copy()
+    Gbad[1, 2] = -1e-6
+    assert lib.xbar_assemble(4, 4, Gbad.ctypes.data, 1, 1, 1, 1, None, ctypes.byref(h)) == xbar.XBAR_EINVAL
+    assert b"G[6]" in lib.xbar_last_error()
+    assert lib.xbar_factor(None, 0) == xbar.XBAR_EINVAL
+    assert lib.xbar_solve(None, 1, None, None, None, None, 1e-8, 4, None) == xbar.XBAR_EINVAL
+    assert lib.xbar_destroy(None) == xbar.XBAR_OK

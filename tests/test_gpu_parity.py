@@ -1,0 +1,191 @@
+"""GPU parity: libxbar (through its C ABI) against the CPU FP64 oracle, element by element.
+
+Bars (relative current error, max over all (b, j) of |I - I*| / |I*|):
+  * XBAR_FP64       <= 1e-10
+  * XBAR_FP32_IR    <= 1e-8 (refinement tolerance 1e-9 so the bar is met with margin)
+Node voltages are compared with a tolerance relative to max V.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_19993_gb300 import inputs, xbar
+from tests.gpu_common import case, oracle_factor, oracle_transfer, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_BAR = 1e-10
+MIXED_BAR = 1e-8
+IR_TOL = 1e-9
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _solve_gpu(G, R, V, precision, voltages=False, tol=IR_TOL, max_iter=10, host=False):
+    M, N = G.shape
+    B = V.shape[0]
+    if host:
+        Gt, Vt = np.ascontiguousarray(G), np.ascontiguousarray(V)
+        I = np.zeros((B, N))
+        vW = np.zeros((B, M, N)) if voltages else None
+        vB = np.zeros((B, M, N)) if voltages else None
+    else:
+        Gt, Vt = _dev(G), _dev(V)
+        I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+        vW = torch.zeros((B, M, N), dtype=torch.float64, device="cuda") if voltages else None
+        vB = torch.zeros((B, M, N), dtype=torch.float64, device="cuda") if voltages else None
+    xb = xbar.Crossbar.assemble(Gt, *R)
+    xb.factor(precision)
+    _, info = xb.solve(Vt, I, vW, vB, tol=tol, max_iter=max_iter)
+    xb.sync()
+    out = {"I": I if host else I.cpu().numpy(), "info": info}
+    if voltages:
+        out["vWL"] = vW if host else vW.cpu().numpy()
+        out["vBL"] = vB if host else vB.cpu().numpy()
+    xb.destroy()
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# small workloads: every output against direct oracle substitution
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,bar", [("fp64", FP64_BAR), ("fp32_ir", MIXED_BAR)])
+def test_xbar16_against_oracle(precision, bar):
+    w = inputs.WORKLOADS["xbar16_fp64"]
+    G, V = inputs.workload_inputs("xbar16_fp64")
+    R = w.circuits[0].as_tuple()
+    ref = oracle.solve(w.M, w.N, G, *R, V, voltages=True)
+    out = _solve_gpu(G, R, V, precision, voltages=True)
+    assert rel_err(out["I"], ref["I"]) <= bar
+    vtol = bar * 0.5
+    assert np.max(np.abs(out["vWL"] - ref["vWL"])) <= vtol
+    assert np.max(np.abs(out["vBL"] - ref["vBL"])) <= vtol
+
+
+@pytest.mark.parametrize("r_wire", [0.5, 2.5, 10.0])
+@pytest.mark.parametrize("precision,bar", [("fp64", FP64_BAR), ("fp32_ir", MIXED_BAR)])
+def test_xbar64_rsweep_against_oracle(r_wire, precision, bar):
+    w = inputs.WORKLOADS["xbar64_rsweep_fp64"]
+    G, V = inputs.workload_inputs("xbar64_rsweep_fp64")
+    R = (1.0, r_wire, r_wire, 10.0)
+    _, f = oracle_factor(w.M, w.N, R)
+    ref = oracle.solve_factored(f, V, nthreads=0)
+    out = _solve_gpu(G, R, V, precision)
+    err = rel_err(out["I"], ref["I"])
+    assert err <= bar, err
+
+
+# ---------------------------------------------------------------------------------------------
+# ragged shapes and edge cases
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("M,N,B", [(1, 1, 1), (1, 7, 5), (9, 1, 3), (5, 7, 37), (17, 33, 19), (33, 17, 200),
+                                   (40, 3, 1000), (3, 40, 9), (100, 20, 65)])
+@pytest.mark.parametrize("precision,bar", [("fp64", FP64_BAR), ("fp32_ir", MIXED_BAR)])
+def test_ragged_shapes(M, N, B, precision, bar):
+    G, V = case(M, N, B, None, seed=M * 1000 + N)
+    R = (1.0, 2.0, 1.5, 10.0)
+    ref = oracle.solve(M, N, G, *R, V, voltages=True)
+    out = _solve_gpu(G, R, V, precision, voltages=True)
+    assert rel_err(out["I"], ref["I"]) <= bar
+    assert np.max(np.abs(out["vWL"] - ref["vWL"])) <= bar
+    assert np.max(np.abs(out["vBL"] - ref["vBL"])) <= bar
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+def test_host_pointers_match_device_pointers(precision):
+    G, V = case(24, 20, 50, None, seed=3)
+    R = (1.0, 1.0, 1.0, 10.0)
+    a = _solve_gpu(G, R, V, precision, voltages=True, host=False)
+    b = _solve_gpu(G, R, V, precision, voltages=True, host=True)
+    np.testing.assert_array_equal(a["I"], b["I"])
+    np.testing.assert_array_equal(a["vBL"], b["vBL"])
+
+
+def test_zero_inputs_and_extreme_conductances():
+    M, N = 12, 10
+    R = (1.0, 1.0, 1.0, 10.0)
+    G = np.zeros((M, N))
+    G[3, 4] = 1e-2
+    V = np.zeros((4, M))
+    V[1] = 0.5
+    V[2, 3] = 1.0
+    ref = oracle.solve(M, N, G, *R, V)
+    for precision in ["fp64", "fp32_ir"]:
+        out = _solve_gpu(G, R, V, precision)
+        # rows of V that are zero give exactly zero currents
+        assert np.all(out["I"][0] == 0.0) and np.all(out["I"][3] == 0.0)
+        nz = np.abs(ref["I"]) > 0
+        assert np.max(np.abs(out["I"][nz] - ref["I"][nz]) / np.abs(ref["I"][nz])) <= MIXED_BAR
+
+
+def test_linearity_and_kirchhoff_on_gpu():
+    """Properties that hold at any size, checked on the GPU result itself."""
+    M, N, B = 48, 40, 64
+    G, V = case(M, N, B, None, seed=11)
+    R = (1.0, 2.5, 2.5, 10.0)
+    V2 = np.concatenate([V, 2.0 * V[:8] - 0.5 * V[8:16]], axis=0)
+    out = _solve_gpu(G, R, V2, "fp64", voltages=True)
+    I = out["I"]
+    np.testing.assert_allclose(I[B:], 2.0 * I[:8] - 0.5 * I[8:16], rtol=1e-10, atol=1e-18)
+    Isrc = (V2 - out["vWL"][:, :, 0]) / R[0]
+    np.testing.assert_allclose(Isrc.sum(1), I.sum(1), rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------------------------
+# full 256 x 256, 8192-vector workload: all currents against the oracle's transfer matrix,
+# a sample of vectors against direct oracle substitution (including node voltages)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,bar", [("fp32_ir", MIXED_BAR), ("fp64", FP64_BAR)])
+def test_xbar256_full_size(precision, bar):
+    w = inputs.WORKLOADS["xbar256_mixed"]
+    G, V = inputs.workload_inputs("xbar256_mixed")
+    R = w.circuits[0].as_tuple()
+    Geff = oracle_transfer(w.M, w.N, R)
+    Iref = V @ Geff
+    out = _solve_gpu(G, R, V, precision, tol=IR_TOL)
+    assert rel_err(out["I"], Iref) <= bar
+    if precision == "fp32_ir":
+        assert 1 <= out["info"]["iters"] <= 4
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(w.B, size=6, replace=False))
+    _, f = oracle_factor(w.M, w.N, R)
+    direct = oracle.solve_factored(f, V[sample])
+    assert rel_err(out["I"][sample], direct["I"]) <= bar
+    assert rel_err(Iref[sample], direct["I"]) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# error paths: status codes, no GPU fault
+# ---------------------------------------------------------------------------------------------
+def test_error_codes():
+    G, V = case(8, 8, 4, None)
+    Gd, Vd = _dev(G), _dev(V)
+    I = torch.zeros((4, 8), dtype=torch.float64, device="cuda")
+    xb = xbar.Crossbar.assemble(Gd, 1.0, 1.0, 1.0, 10.0)
+    st, _ = xb.solve(Vd, I, raise_on_error=False)
+    assert st == xbar.XBAR_ESTATE
+    with pytest.raises(xbar.XbarError):
+        xb.factor(7)
+    xb.factor("fp32_ir")
+    st, _ = xb.solve(Vd, I, max_iter=0, raise_on_error=False)
+    assert st == xbar.XBAR_EINVAL
+    st, info = xb.solve(Vd[:0], I[:0], raise_on_error=False)
+    assert st == xbar.XBAR_OK and info["iters"] == 0
+    xb.destroy()
+
+
+def test_not_converged_is_reported():
+    """One refinement step with an unreachable tolerance must return XBAR_ENOTCONV, not a wrong answer."""
+    w = inputs.WORKLOADS["xbar64_rsweep_fp64"]
+    G, V = inputs.workload_inputs("xbar64_rsweep_fp64", B=16)
+    xb = xbar.Crossbar.assemble(_dev(G), 1.0, 10.0, 10.0, 10.0)
+    xb.factor("fp32_ir")
+    I = torch.zeros((16, w.N), dtype=torch.float64, device="cuda")
+    st, info = xb.solve(_dev(V), I, tol=0.0, max_iter=1, raise_on_error=False)
+    assert st == xbar.XBAR_ENOTCONV
+    assert info["iters"] == 1 and info["max_rel_dI"] > 0
+    xb.destroy()
