@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=64, help="vectors the CPU oracle substitutes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="override the workload's batch size (profiling runs)")
     return ap.parse_args()
 
 
@@ -185,7 +186,7 @@ def run_xbar(args):
     rank, world, local = d.rank, d.world, d.local
     torch.cuda.set_device(local)
     w = inputs.WORKLOADS[args.workload]
-    M, N, B = w.M, w.N, w.B
+    M, N, B = w.M, w.N, (args.batch or w.B)
     R = w.circuits[0].as_tuple()
     G, V = inputs.crossbar(M, N, B, seed=w.seed + rank, g_lo=w.g_lo, g_hi=w.g_hi, v_max=w.v_max)
     stream = torch.cuda.current_stream()
@@ -297,8 +298,8 @@ def run_xbar(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refinement", "data": "synthetic",
-        "config": {"workload": args.workload, "M": M, "N": N, "B": B, "R_s": R[0], "R_w": R[1], "R_b": R[2],
-                   "R_sense": R[3], "precision": "fp32 factor+sweeps, fp64 residual/update", "tol": TOL,
+        "config": {"workload": args.workload + (f"_B{B}" if args.batch else ""), "M": M, "N": N, "B": B,
+                   "R_s": R[0], "R_w": R[1], "R_b": R[2], "R_sense": R[3], "precision": "fp32 factor+sweeps, fp64 residual/update", "tol": TOL,
                    "step": "set_conductances + factor + solve (all refinement)",
                    "l2": "working set per step (>6 GB) exceeds the 129 MB L2", "parallelism": f"replicas{world}"},
         "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.fp64_steps,

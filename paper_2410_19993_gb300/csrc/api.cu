@@ -259,8 +259,10 @@ static xbar_status do_factor(xbar_t h, bool equilibrate) {
   const int Mp = m.Mp, N = m.N;
   const int PB = factor_panel_width<T>();
   int bpm;
+  // FP64 needs many SMs (the FP64 pipe is 1/64 of FP32); FP32 is latency-bound, so fewer blocks
+  // (cheaper cross-block barriers) with 16 rows each
   if (Mp <= 32) bpm = 1;
-  else bpm = std::min(h->nsm, Mp / (sizeof(T) == 8 ? 2 : 4));
+  else bpm = std::min(h->nsm, Mp / (sizeof(T) == 8 ? 2 : 16));
   if (bpm < 1) bpm = 1;
   XB_CUDA(ensure(h->A, h->X, (size_t)N * Mp * Mp * sizeof(T)));
   XB_CUDA(ensure(h->A, h->fsig, 2 * (size_t)Mp * sizeof(T)));

@@ -55,7 +55,7 @@ __device__ __forceinline__ bool group_barrier(unsigned* bar, unsigned nblocks, u
       } else {
         const uint64_t t0 = globaltimer_ns();
         while (*vgen == gen) {
-          __nanosleep(64);
+          __nanosleep(16);
           if (globaltimer_ns() - t0 > limit_ns) {
             ok = 0;
             set_status(status, XBAR_DEV_TIMEOUT);

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kFactorThreads)
   T* sigv = W + R * PB;                       // [Mp]
   T* sgm = sigv + Mp;                         // [R] sigma_j of own rows
   __shared__ unsigned flag;
+  __shared__ T rinv_s;
 
   const uint64_t limit = XBAR_WAIT_LIMIT_NS;
   const T gw = (T)p.gw;
@@ -163,28 +164,34 @@ __global__ void __launch_bounds__(kFactorThreads)
       for (int t = tid; t < PB * Mp; t += kFactorThreads) pn[t] = ld_cg(pb + t);
       __syncthreads();
       for (int t = tid; t < PB * PB; t += kFactorThreads) D[t] = pn[(size_t)(t / PB) * Mp + P0 + t % PB];
-      // invert the pivot block in place (scalar sweep operator, no pivoting)
+      // invert the pivot block in place (scalar sweep operator, no pivoting).  The reciprocal of
+      // each pivot is formed once, by the thread that owns that diagonal entry.
+      if (tid == 0) rinv_s = (T)1 / D[0];
       for (int q = 0; q < PB; ++q) {
         __syncthreads();
-        T nv[(PB * PB + kFactorThreads - 1) / kFactorThreads];
-        const T piv = D[q * PB + q];
+        constexpr int PER = (PB * PB + kFactorThreads - 1) / kFactorThreads;
+        T nv[PER];
+        const T ri = rinv_s;
 #pragma unroll
-        for (int u = 0; u < (PB * PB + kFactorThreads - 1) / kFactorThreads; ++u) {
+        for (int u = 0; u < PER; ++u) {
           const int t = tid + u * kFactorThreads;
           if (t < PB * PB) {
             const int a = t / PB, b = t % PB;
             const T aq = D[a * PB + q], qb = D[q * PB + b], v = D[t];
-            if (a == q && b == q) nv[u] = (T)1 / piv;
-            else if (a == q) nv[u] = qb / piv;
-            else if (b == q) nv[u] = -aq / piv;
-            else nv[u] = v - aq * qb / piv;
+            if (a == q && b == q) nv[u] = ri;
+            else if (a == q) nv[u] = qb * ri;
+            else if (b == q) nv[u] = -aq * ri;
+            else nv[u] = v - aq * qb * ri;
           }
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < (PB * PB + kFactorThreads - 1) / kFactorThreads; ++u) {
+        for (int u = 0; u < PER; ++u) {
           const int t = tid + u * kFactorThreads;
-          if (t < PB * PB) D[t] = nv[u];
+          if (t < PB * PB) {
+            D[t] = nv[u];
+            if (q + 1 < PB && t == (q + 1) * (PB + 1)) rinv_s = (T)1 / nv[u];
+          }
         }
       }
       __syncthreads();

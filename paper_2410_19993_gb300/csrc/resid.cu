@@ -55,26 +55,28 @@ __global__ void resid_kernel(ResidParams p) {
   const size_t base = (size_t)j * p.Mp;
   const bool has_l = j > 0, has_r = j + 1 < p.N;
   const bool src = (j == 0) && (b < p.B);
-  double u = 0.0, rmax = 0.0;
+  double u = 0.0;
+  float rmax = 0.0f;  // |r| tracked in FP32: only its magnitude is reported
+  const size_t col = (size_t)p.Mp * p.Bpad;
   for (int i = p.M - 1; i >= 0; --i) {
     const size_t o = (base + i) * p.Bpad + b;
     u = fma(p.thc[base + i], u, p.phi[o]);  // u_i = phi_i + thc_i u_{i+1}
     const double wi = p.w[o];
-    double nb = 0.0;
-    if (has_l) nb += p.w[o - (size_t)p.Mp * p.Bpad];
-    if (has_r) nb += p.w[o + (size_t)p.Mp * p.Bpad];
+    double nb = has_l ? p.w[o - col] : 0.0;
+    if (has_r) nb = has_l ? nb + p.w[o + col] : p.w[o + col];
     double r = src ? p.gs * p.V[(size_t)b * p.M + i] : 0.0;
     r = fma(p.gw, nb, r);
     r = fma(p.Gc[base + i], u, r);
     r = fma(-p.dW[base + i], wi, r);
-    rmax = fmax(rmax, fabs(r));
-    p.rhat[o] = (float)r * p.s32[base + i];
+    const float rf = (float)r;
+    rmax = fmaxf(rmax, fabsf(rf));
+    p.rhat[o] = rf * p.s32[base + i];
   }
-  if (!(rmax <= 1e300)) set_status(p.status, XBAR_DEV_NONFINITE);
+  if (!(rmax <= 3.0e38f)) set_status(p.status, XBAR_DEV_NONFINITE);
   // block max of |r| then one atomic (non-negative doubles order like their bit patterns)
-  for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+  for (int off = 16; off > 0; off >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
   if ((threadIdx.x & 31) == 0 && p.rmax)
-    atomicMax(p.rmax, (unsigned long long)__double_as_longlong(rmax));
+    atomicMax(p.rmax, (unsigned long long)__double_as_longlong((double)rmax));
 }
 
 // bit-line voltages u = T^-1 (G o w), written over the scratch array `u`

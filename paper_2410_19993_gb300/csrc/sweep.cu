@@ -59,6 +59,18 @@ int sweep_panel_width(int Mp, int B, int nsm) {
   return bp;
 }
 
+// n consecutive elements from 16-byte aligned shared memory with 16-byte loads
+template <typename T, int n>
+__device__ __forceinline__ void load_vec(T (&r)[n], const T* p) {
+  static_assert((n * sizeof(T)) % 16 == 0, "vector width");
+  constexpr int per = 16 / sizeof(T);
+#pragma unroll
+  for (int q = 0; q < n / per; ++q) {
+    const float4 v = *reinterpret_cast<const float4*>(p + q * per);
+    memcpy(&r[q * per], &v, 16);
+  }
+}
+
 template <typename T, int TR, int TC>
 __global__ void sweep_kernel(SweepParams<T> p, int KC) {
   const int Mp = p.Mp, N = p.N, Bp = p.Bp, Bpad = p.Bpad;
@@ -143,10 +155,8 @@ __global__ void sweep_kernel(SweepParams<T> p, int KC) {
 #pragma unroll 4
       for (int k = 0; k < KC; ++k) {
         T xr[TR], vr[TC];
-#pragma unroll
-        for (int a = 0; a < TR; ++a) xr[a] = xb[(size_t)k * Mp + i0 + a];
-#pragma unroll
-        for (int b = 0; b < TC; ++b) vr[b] = vb[(size_t)k * Bp + c0 + b];
+        load_vec<T, TR>(xr, xb + (size_t)k * Mp + i0);
+        load_vec<T, TC>(vr, vb + (size_t)k * Bp + c0);
 #pragma unroll
         for (int a = 0; a < TR; ++a)
 #pragma unroll
