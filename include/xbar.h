@@ -158,6 +158,29 @@ xbar_status xbar_profile_enable(xbar_t h, int enable);
  * (out may not be NULL); reset != 0 clears the accumulators afterwards. */
 xbar_status xbar_profile_read(xbar_t h, xbar_profile* out, int reset);
 
+/*
+ * xbar_solve_noalloc -- the substitution of xbar_solve for a handle factored
+ * with XBAR_FP64, for callers that must not allocate device memory while they
+ * solve (for example a latency-critical loop in which cudaMalloc/cudaFree
+ * could implicitly synchronise the device, or a process whose device memory is
+ * owned by a framework allocator that forbids allocations outside its pool).
+ * The paper has no counterpart: this is a memory-management variant only.
+ *   B   number of input vectors, >= 0.
+ *   V   B x M input voltages, device memory.
+ *   I   B x N bit-line currents (output), device memory.
+ * The kernel's scratch (N x Mp x Bpad doubles, Mp = M rounded up to 16, Bpad
+ * = B rounded up to the kernel's panel width) lives in a fixed 64 MiB device
+ * array inside libxbar that every GPU loading the library keeps until exit;
+ * larger requests fail with XBAR_EINVAL and a message giving the sizes.
+ * Nothing is allocated or freed.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array, so calls whose work overlaps
+ * on the GPU race on it.  Work is asynchronous on the handle's stream.
+ * Errors: XBAR_ESTATE (not factored with XBAR_FP64), XBAR_EINVAL (NULL or host
+ * pointers, B < 0, scratch too large), XBAR_ECUDA.
+ */
+xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I);
+
 /* Wait for the handle's stream and report any device-recorded error. */
 xbar_status xbar_sync(xbar_t h);
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -597,5 +598,93 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
     XB_CUDA(launch_assemble(m, Gd, h->st));
   }
   if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
+  return XBAR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// xbar_solve_noalloc: the FP64 substitution with its scratch in a fixed device array
+// ---------------------------------------------------------------------------------------------
+// Some callers must not allocate device memory while they solve: a latency-critical loop in which
+// cudaMalloc/cudaFree could implicitly synchronise the device and stall it, or a process whose
+// device memory is owned by a framework allocator that forbids allocations outside its pool.
+// For them this entry point runs the same forward/back substitution kernel as xbar_solve on an
+// XBAR_FP64-factored handle, but takes the kernel's scratch (the forward-sweep results, N x Mp x
+// Bpad doubles) from the file-scope array below instead of the handle's growable workspace.  It
+// calls no cudaMalloc, cudaFree or allocating library routine.
+//
+// The array is a fixed XBAR_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU that loads the library and
+// stays reserved until the process exits.  Host code cannot use the array's name as an address (it
+// names a host-side stand-in), so the device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, on the first call that uses the device; make
+// that first call before any stream capture.  All calls share the one array: calls whose work
+// overlaps on the GPU race on it.  Its contents are whatever the last call left; the kernel writes
+// every scratch element it later reads, so nothing needs clearing.
+#define XBAR_NOALLOC_SCRATCH_BYTES (64ull << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[XBAR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+
+// device address of g_noalloc_scratch on the current device `dev` (looked up once per device)
+cudaError_t noalloc_scratch(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (!h->factored || h->prec != XBAR_FP64)
+    return fail(XBAR_ESTATE, "xbar_solve_noalloc needs a handle factored with XBAR_FP64");
+  if (B < 0) return fail(XBAR_EINVAL, "B=%d < 0", B);
+  if (B == 0) return XBAR_OK;
+  if (!V || !I) return fail(XBAR_EINVAL, "V and I must not be NULL");
+  if (!is_device_ptr(V) || !is_device_ptr(I))
+    return fail(XBAR_EINVAL, "xbar_solve_noalloc takes device pointers only (host buffers would need staging)");
+  XB_CUDA(cudaSetDevice(h->dev));
+  const MapDev& m = h->m;
+  const int Bp = sweep_panel_width<double>(m.Mp, B, h->nsm);
+  const int Bpad = ((B + Bp - 1) / Bp) * Bp;
+  const size_t need = (size_t)m.N * m.Mp * Bpad * sizeof(double);
+  if (need > XBAR_NOALLOC_SCRATCH_BYTES)
+    return fail(XBAR_EINVAL,
+                "xbar_solve_noalloc: N*Mp*Bpad*8 = %zu bytes of scratch exceeds the fixed %llu bytes "
+                "(N=%d, Mp=%d, Bpad=%d); use xbar_solve or a smaller batch",
+                need, (unsigned long long)XBAR_NOALLOC_SCRATCH_BYTES, m.N, m.Mp, Bpad);
+  void* scratch = nullptr;
+  {
+    cudaError_t e = noalloc_scratch(h->dev, &scratch);
+    if (e != cudaSuccess) return fail(XBAR_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+  }
+  SweepParams<double> sp;
+  sp.M = m.M;
+  sp.Mp = m.Mp;
+  sp.N = m.N;
+  sp.B = B;
+  sp.Bp = Bp;
+  sp.Bpad = Bpad;
+  sp.X = (const double*)h->X.p;
+  sp.e = m.e_pl;
+  sp.hs = m.h;
+  sp.src = m.src_pl;
+  sp.V = V;
+  sp.rhs = nullptr;
+  sp.z = (double*)scratch;
+  sp.w = nullptr;
+  sp.I = I;
+  sp.accumulate = 0;
+  sp.max_rel = nullptr;
+  sp.status = h->status;
+  XB_CUDA(launch_sweep<double>(sp, h->st));
   return XBAR_OK;
 }

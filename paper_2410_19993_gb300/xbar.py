@@ -72,13 +72,14 @@ def load(build_if_missing: bool = True):
                                ctypes.POINTER(SolveInfo)]
     lib.xbar_sync.argtypes = [_vp]
     lib.xbar_set_conductances.argtypes = [_vp, _vp]
+    lib.xbar_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     lib.xbar_profile_enable.argtypes = [_vp, ctypes.c_int]
     lib.xbar_profile_read.argtypes = [_vp, ctypes.POINTER(Profile), ctypes.c_int]
     lib.xbar_destroy.argtypes = [_vp]
     lib.xbar_last_error.restype = ctypes.c_char_p
     lib.xbar_version.restype = ctypes.c_char_p
     for f in ("xbar_assemble", "xbar_factor", "xbar_solve", "xbar_sync", "xbar_destroy", "xbar_set_conductances",
-              "xbar_profile_enable", "xbar_profile_read"):
+              "xbar_profile_enable", "xbar_profile_read", "xbar_solve_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -141,6 +142,13 @@ class Crossbar:
         if raise_on_error:
             _check(st)
         return st, info.as_dict()
+
+    def solve_noalloc(self, V, I, raise_on_error=True):
+        """xbar_solve_noalloc: FP64 substitution with library-internal fixed scratch (device V, I only)."""
+        st = load().xbar_solve_noalloc(self.handle, int(V.shape[0]), _ptr(V), _ptr(I))
+        if raise_on_error:
+            _check(st)
+        return st
 
     def set_conductances(self, G):
         _check(load().xbar_set_conductances(self.handle, _ptr(G)))
