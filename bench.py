@@ -277,9 +277,16 @@ def run_xbar(args):
     dom = max(per_step, key=lambda ph: per_step[ph]["ms"])
     work, _ = algorithmic_work(dom, M, N, B)
     ms_launch = prof[dom]["ms"] / prof[dom]["launches"]
-    peaks = pipe_peaks(measured_peaks().get("sm_max_mhz", 2070.0))
+    mp = measured_peaks()
+    peaks = pipe_peaks(mp.get("sm_max_mhz", 2070.0))
     achieved = work / (ms_launch / 1e3) / 1e12
-    if dom in ("sweep", "factor", "update"):
+    if dom == "sweep" and M <= 256:
+        # tensor-core sweep (tcgen05 kind::tf32, four split products per algorithmic multiply-add)
+        tf32 = mp.get("bf16_tflops", 1936.2) * (1.1 / 2.25)
+        bound, peak, note = "tensor", tf32, ("TF32 dense = measured BF16 burst x nominal TF32/BF16 ratio 1.1/2.25 "
+                                             "(of measured); achieved counts algorithmic flops only, the kernel "
+                                             "issues four TF32 products per multiply-add")
+    elif dom in ("sweep", "factor", "update"):
         bound, peak, note = "alu", peaks["fp32_tflops"], "FP32 FMA pipe, 152 SM x 128 lanes x 2 x max SM clock"
     else:
         bound, peak, note = "alu", peaks["fp64_tflops"], "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock"

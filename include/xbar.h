@@ -116,8 +116,13 @@ xbar_status xbar_factor(xbar_t h, xbar_precision p);
  *   I          B x N bit-line termination currents (output, host or device).
  *   vWL, vBL   B x M x N word-line / bit-line node voltages (outputs, may be
  *              NULL; host or device).
- *   tol        XBAR_FP32_IR only: stop when max |dI|/|I| of a correction is
- *              <= tol (e.g. 1e-8); ignored for XBAR_FP64.
+ *   tol        XBAR_FP32_IR only: target max relative current error (e.g.
+ *              1e-8).  Refinement stops after the correction k whose
+ *              max |dI|/|I| (call it d_k) is <= tol, or, from the second
+ *              correction on, when the observed contraction rho = d_k/d_{k-1}
+ *              is <= 1/2 and d_k rho / (1 - rho) <= tol (the error left after
+ *              applying correction k under linear convergence).  Ignored for
+ *              XBAR_FP64.
  *   max_iter   XBAR_FP32_IR only: most corrections to apply (>= 1).
  *   info       optional diagnostics (may be NULL).
  * Errors: XBAR_ESTATE if not factored; XBAR_EINVAL for B < 0, NULL V or I, or

@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -9,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/xbar.h"
+#include "xbar.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -107,6 +108,8 @@ struct xbar_s {
   unsigned* status = nullptr;
   // factor
   Buf X, fsig, fpbuf, fbar, fparams;
+  Buf Xt;          // tensor-core tiled TF32 hi/lo copy of the FP32 factor
+  int tc_ready = 0;
   // solve workspace
   Buf z, dhat, rhat, w64, phi, maxrel, rmax;
   // staging for host pointers
@@ -254,6 +257,22 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   return XBAR_OK;
 }
 
+// FP32 substitutions run on the tensor cores (sweep_tc.cu) when the block fits (Mp <= 256);
+// XBAR_SWEEP=simt in the environment selects the CUDA-core kernel instead.
+static bool use_tc_sweep(int Mp) {
+  const char* e = getenv("XBAR_SWEEP");
+  if (e && strcmp(e, "simt") == 0) return false;
+  return sweep_tc_supported(Mp);
+}
+
+// FP32 factors run on a thread-block cluster (factor_cluster.cu) when 32 <= Mp <= 256;
+// XBAR_FACTOR=group in the environment selects the cooperative-group kernel instead.
+static bool use_cluster_factor(int Mp) {
+  const char* e = getenv("XBAR_FACTOR");
+  if (e && strcmp(e, "group") == 0) return false;
+  return factor_cluster_supported(Mp);
+}
+
 template <typename T>
 static xbar_status do_factor(xbar_t h, bool equilibrate) {
   MapDev& m = h->m;
@@ -286,8 +305,18 @@ static xbar_status do_factor(xbar_t h, bool equilibrate) {
   fp.bar = (unsigned*)h->fbar.p;
   XB_CUDA(cudaMemsetAsync(h->fbar.p, 0, 2 * sizeof(unsigned), h->st));
   XB_CUDA(cudaMemcpyAsync(h->fparams.p, &fp, sizeof(fp), cudaMemcpyHostToDevice, h->st));
-  PhaseScope ps(h, XBAR_PHASE_FACTOR);
-  XB_CUDA(launch_factor<T>((const FactorParams<T>*)h->fparams.p, 1, Mp, bpm, h->status, h->st));
+  PhaseScope ps(h, XBAR_PHASE_FACTOR, sizeof(T) == 4 && use_tc_sweep(Mp) ? 2 : 1);
+  if (sizeof(T) == 4 && use_cluster_factor(Mp))
+    XB_CUDA(launch_factor_cluster((const FactorParams<float>*)h->fparams.p, 1, Mp, h->status, h->st));
+  else
+    XB_CUDA(launch_factor<T>((const FactorParams<T>*)h->fparams.p, 1, Mp, bpm, h->status, h->st));
+  h->tc_ready = 0;
+  if (sizeof(T) == 4 && use_tc_sweep(Mp)) {
+    const int Mt = sweep_tc_rows(Mp);
+    XB_CUDA(ensure(h->A, h->Xt, (size_t)N * Mt * Mt * 2 * sizeof(float)));
+    XB_CUDA(launch_sweep_tc_tile((const float*)h->X.p, (float*)h->Xt.p, Mp, N, h->st));
+    h->tc_ready = 1;
+  }
   return XBAR_OK;
 }
 
@@ -352,7 +381,9 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     dvBL = (double*)h->svBL.p;
   }
 
-  const int Bp = mixed ? sweep_panel_width<float>(Mp, B, h->nsm) : sweep_panel_width<double>(Mp, B, h->nsm);
+  const bool tc = mixed && h->tc_ready;
+  const int Bp = tc ? kSweepTcPanel
+                    : (mixed ? sweep_panel_width<float>(Mp, B, h->nsm) : sweep_panel_width<double>(Mp, B, h->nsm));
   const int nblk = (B + Bp - 1) / Bp;
   const int Bpad = nblk * Bp;
   const size_t nst = (size_t)N * Mp * Bpad;
@@ -444,7 +475,8 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     sp.status = h->status;
     {
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
-      XB_CUDA(launch_sweep<float>(sp, st));     // x0 = solve32(b)
+      if (tc) XB_CUDA(launch_sweep_tc(sp, (const float*)h->Xt.p, st));  // x0 = solve32(b)
+      else XB_CUDA(launch_sweep<float>(sp, st));
     }
     {
       PhaseScope ps(h, XBAR_PHASE_UPDATE);
@@ -465,8 +497,9 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       sp.accumulate = 1;
       sp.max_rel = (float*)h->maxrel.p;
       {
-        PhaseScope ps(h, XBAR_PHASE_SWEEP);
-        XB_CUDA(launch_sweep<float>(sp, st));   // dhat = solve32(rhat), I += dI
+        PhaseScope ps(h, XBAR_PHASE_SWEEP);     // dhat = solve32(rhat), I += dI
+        if (tc) XB_CUDA(launch_sweep_tc(sp, (const float*)h->Xt.p, st));
+        else XB_CUDA(launch_sweep<float>(sp, st));
       }
       w_current = false;
       ++iters;
@@ -478,7 +511,11 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       prev = last;
       last = mr;
       if (!(mr == mr)) break;                   // NaN: give up, reported below
-      if (mr <= tol) {
+      // converged when this correction is within tol, or when the observed linear contraction
+      // rate rho = |dI_k| / |dI_{k-1}| bounds what remains after applying it:
+      // |dI_k| rho / (1 - rho) <= tol (rho <= 1/2, at least two corrections)
+      const double rho = (it >= 1 && prev > 0.0) ? (double)mr / prev : 1.0;
+      if (mr <= tol || (rho <= 0.5 && (double)mr * rho / (1.0 - rho) <= tol)) {
         converged = true;
         break;
       }

@@ -132,6 +132,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
+// non-suspending probe of phase `parity`
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded spin on phase `parity` with test_wait (no suspension, so the waiter resumes as soon as
+// the phase completes); sleep_ns > 0 backs off between probes for waiters that are not latency
+// critical.  false (and XBAR_DEV_TIMEOUT) on expiry.
+__device__ __forceinline__ bool mbar_spin_bounded(uint64_t* bar, unsigned parity, unsigned* status,
+                                                  uint64_t limit_ns, unsigned sleep_ns) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned k = 0;
+  while (!mbar_test_wait(bar, parity)) {
+    if (sleep_ns) __nanosleep(sleep_ns);
+    if ((++k & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+      set_status(status, XBAR_DEV_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
 // atomic max for non-negative floats through their ordered bit patterns
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
   if (!(v >= 0.0f)) v = __int_as_float(0x7f800000);  // NaN -> +inf so it is noticed

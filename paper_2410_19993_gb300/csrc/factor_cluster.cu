@@ -1,0 +1,273 @@
+// factor_cluster.cu -- the block Thomas factorization of factor.cu on a thread-block cluster.
+//
+// Same mathematics as factor.cu (Z_0 = C_0, Z_j = C_j - g_w^2 X_{j-1}, X_j = Z_j^{-1}, diagonals
+// from the grounded row sums sigma_j), for FP32 factors with 32 <= Mp <= 256.  A cluster of C blocks owns
+// one map; block g holds rows [g R, (g+1) R) of the current matrix in shared memory (R = 16, C = Mp / R).
+// The in-place blocked Gauss-Jordan inversion uses panels of R rows, so panel p is exactly block p's
+// rows: the owner inverts its R x R pivot block, forms the new panel rows and publishes them to a
+// double-buffered global (L2-resident) buffer; one hardware cluster barrier (release/acquire at
+// cluster scope) orders the exchange, and every other block reads the panel from L2 and updates its
+// own rows.  (Pulling the panel from the owner's shared memory instead makes all peers drain one
+// SM's shared-memory port at once and is several times slower.)  One cluster barrier per panel plus
+// one per column step, and no software spin-wait: every block executes the same barrier sequence.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace xbar {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRows = 16;
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace
+
+// dynamic shared memory: rows [R][Mp], pn [R][Mp], D [2][R][R], W [R][R], sigv [Mp], sv [Mp],
+// ev [Mp], sg [2][R], rinv [64]
+size_t factor_cluster_smem_bytes(int Mp, int R) {
+  return ((size_t)2 * R * Mp + 3 * (size_t)R * R + 3 * (size_t)Mp + 2 * R + 64) * sizeof(float);
+}
+
+// acc[r] (r < 16) += sign * sum_m coef[r*16 + m] * col[m], coefficients read as 16-byte broadcasts
+__device__ __forceinline__ void rank16_update(float (&acc)[16], const float* __restrict__ coef,
+                                              const float (&col)[16], float sign) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const float4* c4 = reinterpret_cast<const float4*>(coef + r * 16);
+    float a = acc[r];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 c = c4[q];
+      a = fmaf(sign * c.x, col[4 * q], a);
+      a = fmaf(sign * c.y, col[4 * q + 1], a);
+      a = fmaf(sign * c.z, col[4 * q + 2], a);
+      a = fmaf(sign * c.w, col[4 * q + 3], a);
+    }
+    acc[r] = a;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    factor_cluster_kernel(const FactorParams<float>* __restrict__ maps, int C, unsigned* status) {
+  constexpr int R = kRows;  // rows per block = panel width
+  const FactorParams<float> p = maps[blockIdx.x / C];
+  const uint32_t g = cluster_rank();
+  const int M = p.M, Mp = p.Mp, N = p.N;
+  const int r0 = (int)g * R;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = kThreads / 32;
+
+  extern __shared__ __align__(16) float sm[];
+  float* rows = sm;                         // [R][Mp]
+  float* pn = rows + (size_t)R * Mp;        // [R][Mp]
+  float* Dm = pn + (size_t)R * Mp;          // [2][R][R]
+  float* W = Dm + 2 * R * R;                // [R][R]
+  float* sigv = W + R * R;                  // [Mp]
+  float* sv = sigv + Mp;                    // [Mp] equilibration scale of column j
+  float* ev = sv + Mp;                      // [Mp] coupling to column j-1
+  float* sg = ev + Mp;                      // [2][R] sigma of own rows, by step parity
+  float* rinv = sg + 2 * R;                 // [64] pivot reciprocals
+
+  if (Mp != C * R || (int)blockDim.x != kThreads) {
+    if (tid == 0) set_status(status, XBAR_DEV_BADLAUNCH);
+    return;  // uniform across the cluster: every block sees the same arguments
+  }
+  const float gw = (float)p.gw;
+
+  for (int j = 0; j < N; ++j) {
+    const double* Cj = p.Coff + (size_t)j * Mp * Mp;
+    const double* sj = p.s ? p.s + (size_t)j * Mp : nullptr;
+    const double* sjm = (p.s && j > 0) ? p.s + (size_t)(j - 1) * Mp : nullptr;
+    const double* ejm = j > 0 ? p.e + (size_t)(j - 1) * Mp : nullptr;
+    const double* hj = p.h + (size_t)j * Mp;
+    if (j + 1 < N)  // warm L2 with the next column's off-diagonal block rows of this block
+      for (int t = tid * 16; t < R * Mp; t += kThreads * 16)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(Cj + (size_t)Mp * Mp + (size_t)r0 * Mp + t));
+
+    for (int k = tid; k < Mp; k += kThreads) {
+      sv[k] = sj ? (float)sj[k] : 1.0f;
+      ev[k] = ejm ? (float)ejm[k] : 0.0f;
+    }
+    // (1) sigma_j of own rows: h_j + g_w S X^_{j-1} S sigma_{j-1}  (X^_{j-1} own rows are in `rows`)
+    if (j > 0) {
+      const float* sp = p.sig + (size_t)((j - 1) & 1) * Mp;
+      for (int k = tid; k < Mp; k += kThreads) sigv[k] = __ldcg(sp + k) * (sjm ? (float)sjm[k] : 1.0f);
+      __syncthreads();
+      for (int r = warp; r < R; r += nwarps) {
+        const int i = r0 + r;
+        float acc = 0.0f;
+        for (int k = lane; k < Mp; k += 32) acc = fmaf(rows[(size_t)r * Mp + k], sigv[k], acc);
+        acc = warp_sum_f(acc);
+        if (lane == 0)
+          sg[(j & 1) * R + r] = (i < M) ? (float)hj[i] + gw * (sjm ? (float)sjm[i] : 1.0f) * acc : 0.0f;
+      }
+    } else {
+      for (int r = tid; r < R; r += kThreads) {
+        const int i = r0 + r;
+        sg[r] = (i < M) ? (float)(hj[i] + p.gsrc) : 0.0f;
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += kThreads) p.sig[(size_t)(j & 1) * Mp + r0 + r] = sg[(j & 1) * R + r];
+
+    // (2) X^_{j-1} own rows to the output
+    if (j > 0) {
+      float* Xo = p.X + (size_t)(j - 1) * Mp * Mp + (size_t)r0 * Mp;
+      for (int t = tid; t < R * Mp; t += kThreads) Xo[t] = rows[t];
+    }
+
+    // (3) Z^_j own rows: off-diagonal, then the subtraction-free diagonal
+    for (int t = tid * 2; t < R * Mp; t += kThreads * 2) {
+      const int r = t / Mp, k = t - r * Mp, i = r0 + r;
+      const double2 c2 = *reinterpret_cast<const double2*>(Cj + (size_t)r0 * Mp + t);
+      const float si = sv[i], ei = ev[i];
+      const float x0 = j > 0 ? rows[t] : 0.0f, x1 = j > 0 ? rows[t + 1] : 0.0f;  // X^_{j-1}
+      float v0 = 0.0f, v1 = 0.0f;
+      if (i < M) {
+        if (k < M && k != i) v0 = si * sv[k] * (float)c2.x - ei * ev[k] * x0;
+        if (k + 1 < M && k + 1 != i) v1 = si * sv[k + 1] * (float)c2.y - ei * ev[k + 1] * x1;
+      }
+      rows[t] = v0;
+      rows[t + 1] = v1;
+    }
+    __syncthreads();
+    for (int r = warp; r < R; r += nwarps) {
+      const int i = r0 + r;
+      float acc = 0.0f;
+      for (int k = lane; k < M; k += 32) acc += fabsf(rows[(size_t)r * Mp + k]) / sv[k];
+      acc = warp_sum_f(acc);
+      if (lane == 0) {
+        float d = 1.0f;
+        if (i < M) {
+          const float si = sv[i];
+          d = si * si * (sg[(j & 1) * R + r] + (j < N - 1 ? gw : 0.0f)) + si * acc;
+        }
+        rows[(size_t)r * Mp + i] = d;
+      }
+    }
+    __syncthreads();
+
+    // (4) blocked Gauss-Jordan inversion; panel p = rows of block p
+    for (int pp = 0; pp < C; ++pp) {
+      const int P0 = pp * R;
+      if ((int)g == pp) {
+        // owner: invert the R x R pivot block (scalar sweep, double-buffered, one reciprocal per pivot)
+        for (int t = tid; t < R * R; t += kThreads) Dm[t] = rows[(size_t)(t / R) * Mp + P0 + t % R];
+        __syncthreads();
+        if (tid == 0) rinv[0] = 1.0f / Dm[0];
+        for (int q = 0; q < R; ++q) {
+          __syncthreads();
+          const float* Dc = Dm + (q & 1) * R * R;
+          float* Dn = Dm + ((q + 1) & 1) * R * R;
+          const float ri = rinv[q];
+          for (int t = tid; t < R * R; t += kThreads) {
+            const int a = t / R, b = t - a * R;
+            float v;
+            if (a == q && b == q) v = ri;
+            else if (a == q) v = Dc[q * R + b] * ri;
+            else if (b == q) v = -Dc[a * R + q] * ri;
+            else v = Dc[t] - Dc[a * R + q] * Dc[q * R + b] * ri;
+            Dn[t] = v;
+            if (q + 1 < R && a == q + 1 && b == q + 1) rinv[q + 1] = 1.0f / v;
+          }
+        }
+        __syncthreads();
+        const float* Dinv = Dm + (R & 1) * R * R;
+        // new panel rows: D x (old panel rows) outside the panel columns, D inside
+        for (int k = tid; k < Mp; k += kThreads) {
+          float col[R], acc[R];
+          const bool kin = (k >= P0 && k < P0 + R);
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            col[m] = rows[(size_t)m * Mp + k];
+            acc[m] = 0.0f;
+          }
+          rank16_update(acc, Dinv, col, 1.0f);
+          float* pub = p.pbuf + (size_t)((j * C + pp) & 1) * R * Mp;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float v = kin ? Dinv[r * R + (k - P0)] : acc[r];
+            rows[(size_t)r * Mp + k] = v;
+            pub[(size_t)r * Mp + k] = v;
+          }
+        }
+      }
+      cluster_sync();  // the owner's new panel rows are visible cluster-wide
+      if ((int)g != pp) {
+        // read the published panel rows (L2) and update own rows:
+        //   row <- (row outside the panel columns) - row[P] . panel
+        const float4* pub = reinterpret_cast<const float4*>(p.pbuf + (size_t)((j * C + pp) & 1) * R * Mp);
+        for (int t = tid; t < R * Mp / 4; t += kThreads) reinterpret_cast<float4*>(pn)[t] = __ldcg(pub + t);
+        for (int t = tid; t < R * R; t += kThreads) W[t] = rows[(size_t)(t / R) * Mp + P0 + t % R];
+        __syncthreads();
+        for (int k = tid; k < Mp; k += kThreads) {
+          float col[R], acc[R];
+          const bool kin = (k >= P0 && k < P0 + R);
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            col[m] = pn[(size_t)m * Mp + k];
+            acc[m] = kin ? 0.0f : rows[(size_t)m * Mp + k];
+          }
+          rank16_update(acc, W, col, -1.0f);
+#pragma unroll
+          for (int r = 0; r < R; ++r) rows[(size_t)r * Mp + k] = acc[r];
+        }
+        __syncthreads();
+      }
+    }
+    cluster_sync();  // every pull of this step's last panel is done before its owner overwrites `rows`
+  }
+  {
+    float* Xo = p.X + (size_t)(N - 1) * Mp * Mp + (size_t)r0 * Mp;
+    for (int t = tid; t < R * Mp; t += kThreads) Xo[t] = rows[t];
+  }
+  cluster_sync();  // no block leaves while another may still read its shared memory
+}
+
+bool factor_cluster_supported(int Mp) { return Mp >= 2 * kRows && Mp <= 16 * kRows && Mp % kRows == 0; }
+
+int factor_cluster_size(int Mp) { return Mp / kRows; }
+
+cudaError_t launch_factor_cluster(const FactorParams<float>* maps_dev, int nmaps, int Mp, unsigned* status,
+                                  cudaStream_t st) {
+  const int C = factor_cluster_size(Mp);
+  const size_t smem = factor_cluster_smem_bytes(Mp, kRows);
+  cudaError_t err = cudaFuncSetAttribute(factor_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  if (C > 8) {
+    err = cudaFuncSetAttribute(factor_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nmaps * C);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, factor_cluster_kernel, maps_dev, C, status);
+}
+
+}  // namespace xbar

@@ -62,6 +62,12 @@ int factor_panel_width();
 template <typename T>
 size_t factor_smem_bytes(int Mp, int rows_per_block);
 
+// FP32 factor on a thread-block cluster (factor_cluster.cu): 32 <= Mp <= 256
+bool factor_cluster_supported(int Mp);
+int factor_cluster_size(int Mp);
+cudaError_t launch_factor_cluster(const FactorParams<float>* maps_dev, int nmaps, int Mp, unsigned* status,
+                                  cudaStream_t st);
+
 // ---- sweeps (forward + back substitution, current extraction) ---------------------------------
 template <typename T>
 struct SweepParams {
@@ -84,6 +90,14 @@ template <typename T>
 cudaError_t launch_sweep(const SweepParams<T>& p, cudaStream_t st);
 template <typename T>
 int sweep_panel_width(int Mp, int B, int nsm);
+
+// ---- tensor-core (tcgen05, 3xTF32) FP32 sweeps: panels of 64 vectors, Mp <= 256 -------------
+bool sweep_tc_supported(int Mp);
+int sweep_tc_rows(int Mp);  // rows of the tiled factor (128 or 256)
+constexpr int kSweepTcPanel = 64;
+// X (FP32 [N][Mp][Mp]) -> Xt: TF32 hi/lo split in the MMA's chunked core-matrix order
+cudaError_t launch_sweep_tc_tile(const float* X, float* Xt, int Mp, int N, cudaStream_t st);
+cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaStream_t st);
 
 // ---- FP64 refinement kernels and node voltages ------------------------------------------------
 struct ResidParams {

@@ -1,0 +1,456 @@
+// sweep_tc.cu -- forward/back substitution on the 5th-generation tensor cores (tcgen05).
+//
+// Same recurrences as sweep.cu (Sec. II-C substitutions after block Thomas):
+//     z_0 = X_0 r_0,  z_j = X_j (r_j + e_{j-1} o z_{j-1});   w_{N-1} = z_{N-1},
+//     w_j = z_j + X_j (e_j o w_{j+1});   I_j = hs_j . w_j,
+// for a panel of 64 input vectors per block.  Each step is D[Mt x 64] = X_j[Mt x Mt] . v[Mt x 64]
+// computed from split TF32 operands (x = x_hi + x_lo, both TF32): with B_hi and B_lo stacked along
+// N, each K step issues A_hi [B_hi | B_lo] and A_lo [B_hi | B_lo] (N = 128) and the epilogue adds
+// the two column halves, so D = (A_hi + A_lo)(B_hi + B_lo) with FP32 accumulation in tensor memory.
+// Dependent accumulations into one TMEM region serialise at ~170 cycles per MMA, so even and odd
+// K steps accumulate into separate regions: 2 row halves x 2 K parities = 4 independent chains., which keeps FP32-level accuracy: a plain TF32
+// product would cost the refinement several extra FP64 residual passes.
+//
+// Operands.  A = X_j, split and pre-tiled in global memory (sweep_tc_tile_kernel) in the
+// no-swizzle K-major core-matrix order of the MMA (8 rows x 16 bytes per core matrix), chunk by
+// chunk of 16 K-elements, hi and lo adjacent, so one 1-D bulk copy per chunk lands MMA-ready data
+// in shared memory.  B = the running vector of the panel, written by the epilogue threads into the
+// same core-matrix order (K-blocks padded by 16 bytes so the stores are bank-conflict free).
+// D = tcgen05 tensor memory, one 64-column slab per 128-row half of X_j.
+//
+// Roles: a producer warp streams the chunks through a ring of stages (one 1-D bulk copy each,
+// completion on mbarriers) as far ahead as free stages allow; thread 0 issues the MMAs and frees
+// each stage with tcgen05.commit; 8 epilogue warps (named barrier 1, which the producer never
+// joins) run the epilogue (tcgen05.ld of D, z/w stores,
+// current dot products by warp transpose-reduction, next-step vector split into hi/lo).  Every
+// wait is bounded; on expiry the block records XBAR_DEV_TIMEOUT, drains and frees its tensor
+// memory before returning.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace xbar {
+
+namespace tc {
+
+constexpr int kBP = 64;       // input vectors per panel (MMA N)
+constexpr int kKC = 8;        // K elements per bulk-copied chunk (one MMA K step)
+constexpr int kThreads = 256;
+// B operand = [v_hi | v_lo] stacked along N (16 core-matrix groups of 8 columns per K block); the
+// 16-byte pad between K blocks keeps the epilogue's stores bank-conflict free
+constexpr uint32_t kLBO_B = 2 * (kBP / 8) * 128 + 16;
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// no-swizzle K-major shared-memory matrix descriptor (tcgen05 format: version 1 in bits 46-47)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// sum over the 32 lanes of column `lane` of v[0..31] (v is destroyed)
+__device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int m = 0; m < w; ++m) {
+      const float send = up ? v[m] : v[m + w];
+      const float keep = up ? v[m + w] : v[m];
+      v[m] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+}  // namespace tc
+
+// X_j (FP32 [N][Mp][Mp]) -> split TF32 hi/lo in the MMA's chunked core-matrix order
+// Xt[j][kc][part][cl][g][r][e], kc < Mt/16, part 0 = hi / 1 = lo, cl < 4, g < Mt/8, r < 8, e < 4;
+// element (row n, column k) of X_j with n = 8g + r, k = 16 kc + 4 cl + e; rows/cols >= Mp are zero.
+__global__ void sweep_tc_tile_kernel(const float* __restrict__ X, float* __restrict__ Xt, int Mp, int Mt, int N) {
+  const size_t per = (size_t)Mt * Mt;
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= per * N) return;
+  const int j = (int)(idx / per);
+  const int rem = (int)(idx - (size_t)j * per);
+  const int n = rem / Mt, k = rem - n * Mt;
+  const float x = (n < Mp && k < Mp) ? X[((size_t)j * Mp + n) * Mp + k] : 0.0f;
+  const float hi = tc::tf32_rna(x);
+  const float lo = tc::tf32_rna(x - hi);
+  const int kc = k / tc::kKC, kl = k % tc::kKC, cl = kl / 4, e = kl % 4, g = n / 8, r = n % 8;
+  const size_t part = (size_t)(tc::kKC / 4) * (Mt / 8) * 32;  // floats in one part of a chunk
+  const size_t base = ((size_t)j * (Mt / tc::kKC) + kc) * 2 * part;
+  const size_t off = ((size_t)cl * (Mt / 8) + g) * 32 + r * 4 + e;
+  Xt[base + off] = hi;
+  Xt[base + part + off] = lo;
+}
+
+// named barrier over the 8 epilogue warps (the producer warp never joins it)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool epi_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; }
+
+__global__ void __launch_bounds__(tc::kThreads + 32, 1)
+    sweep_tc_kernel(SweepParams<float> p, const float* __restrict__ Xt, int Mt) {
+  using namespace tc;
+  constexpr int BP = kBP, KC = kKC;
+  const int nh = Mt / 128;
+  const int NS = tc_stages(Mt);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b0 = blockIdx.x * BP;
+  const int N = p.N, Mp = p.Mp, Bpad = p.Bpad;
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);  // [NS]
+  uint64_t* empty = full + 8;                          // [NS]
+  uint64_t* dfull = full + 16;                         // [1]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 17);
+  unsigned* fail = reinterpret_cast<unsigned*>(full + 18);
+  float* red = reinterpret_cast<float*>(smem + 256);   // [8][64]
+  unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
+  const uint32_t part_bytes = (uint32_t)KC * Mt * 4;
+  const uint32_t chunk_bytes = 2 * part_bytes;
+  unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // (Mt/4) K-blocks of kLBO_B bytes: [hi groups | lo groups]
+
+  const int cps = Mt / KC;  // chunks per step
+  const int nsteps = 2 * N - 1;
+  const long long nchunks = (long long)nsteps * cps;
+  // accumulators: per 128-row half and per K parity (even/odd K steps, so four independent MMA
+  // chains keep the tensor pipe busy), 128 columns [X v_hi | X v_lo] each
+  const uint32_t ncols = (uint32_t)(nh * 4 * BP);
+  const uint32_t idesc2 = idesc_tf32(128, 2 * BP);
+  const uint32_t LBO_A = (uint32_t)Mt * 16, SBO = 128;
+
+  if ((int)blockDim.x != kThreads + 32 || (nh != 1 && nh != 2) || b0 + BP > Bpad) {
+    if (tid == 0) set_status(p.status, XBAR_DEV_BADLAUNCH);
+    return;
+  }
+  if (tid == 0) {
+    for (int st = 0; st < NS; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(dfull, 1);
+    *fail = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, ncols);
+    tmem_relinquish();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 8) {
+    // ---- producer: stream X chunks into the stage ring, as far ahead as free stages allow ----
+    if (lane == 0) {
+      long long issued = 0;
+      int st = 0, use = 0, s = 0, kc = 0;  // stage, uses of this stage so far, step, chunk in step
+      for (long long c = 0; c < nchunks; ++c) {
+        if (c >= NS && !mbar_spin_bounded(&empty[st], (unsigned)((use - 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 0))
+          break;
+        issued = c + 1;
+        const int j = s < N ? s : 2 * N - 2 - s;
+        mbar_arrive_expect_tx(&full[st], chunk_bytes);
+        bulk_g2s(xs + (size_t)st * chunk_bytes, Xt + ((size_t)j * cps + kc) * (chunk_bytes / 4), chunk_bytes,
+                 &full[st]);
+        if (++kc == cps) { kc = 0; ++s; }
+        if (++st == NS) { st = 0; ++use; }
+      }
+      // before the block may exit: the last copy into each stage has landed (bounded wait)
+      for (long long c = (issued > NS ? issued - NS : 0); c < issued; ++c)
+        mbar_wait_bounded(&full[c % NS], (unsigned)((c / NS) & 1), p.status, XBAR_WAIT_LIMIT_NS);
+    }
+    __syncwarp();
+  } else {
+    // ---- 8 epilogue warps; thread 0 also issues the MMAs ---------------------------------------
+    // mapping: warp -> TMEM lane quarter q and either a 128-row half (nh = 2, all 64 columns)
+    // or a 32-column half (nh = 1, rows 0..127)
+    const int q = warp & 3, sub = warp >> 2;
+    const int h = (nh == 2) ? sub : 0;
+    const int cb = (nh == 2) ? 0 : sub * 32;
+    const int ncb = (nh == 2) ? 2 : 1;
+    const int i = h * 128 + q * 32 + lane;
+    const bool real = i < Mp;
+
+    // B-operand byte offset of (node i, column col): K block i/4, N group col/8, row col%8, element i%4
+    unsigned char* vrow = vb + (uint32_t)(i >> 2) * kLBO_B + (uint32_t)(i & 3) * 4;
+    auto put_v = [&](int col, float v) {
+      const float hi = tf32_rna(v);
+      const float lo = tf32_rna(v - hi);
+      unsigned char* a = vrow + (uint32_t)(col >> 3) * 128 + (uint32_t)(col & 7) * 16;
+      *reinterpret_cast<float*>(a) = hi;
+      *reinterpret_cast<float*>(a + (kBP / 8) * 128) = lo;
+    };
+
+    for (int blk = 0; blk < ncb; ++blk)
+      for (int n = 0; n < 32; ++n) {
+        const int col = cb + blk * 32 + n, b = b0 + col;
+        float v = 0.0f;
+        if (p.V) {
+          if (i < p.M && b < p.B) v = p.src[i] * (float)p.V[(size_t)b * p.M + i];
+        } else if (real) {
+          v = p.rhs[(size_t)i * Bpad + b];
+        }
+        put_v(col, v);
+      }
+    fence_proxy_async_smem();
+    fence_before();
+    epi_sync();
+
+    // MMA-issuer state (thread 0): stage ring position and descriptors of every stage/half
+    // (descriptor address fields are the low bits, so stage / half / lo offsets are plain adds)
+    int mst = 0, muse = 0;
+    const uint64_t adesc0 = sdesc(smem_addr(xs), LBO_A, SBO);
+    const uint64_t bdesc0 = sdesc(smem_addr(vb), kLBO_B, SBO);
+    const uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_lo = part_bytes >> 4;
+    float local_max = 0.0f;
+    for (int s = 0; s < nsteps; ++s) {
+      const bool fwd = s < N;
+      const int j = fwd ? s : 2 * N - 2 - s;
+      const bool nfwd = s + 1 < N;
+      // warm L2 with the global operands this step's epilogue will read
+      if (real) {
+        const size_t o = ((size_t)j * Mp + i) * Bpad + b0 + cb;
+        for (int blk = 0; blk < ncb; ++blk) {
+          if (!fwd) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.z + o + blk * 32));
+          if (nfwd && p.rhs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + o + blk * 32 + (size_t)Mp * Bpad));
+        }
+      }
+      // ---- MMA phase: thread 0 ----------------------------------------------------------------
+      if (tid == 0) {
+        fence_after();
+        bool ok = true;
+        uint64_t bdesc = bdesc0;  // advances by one K-step (2 K blocks) per chunk
+        for (int kc = 0; kc < cps; ++kc) {
+          if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t set = (uint32_t)(kc & 1) * (2 * BP);
+          const uint64_t ast = adesc0 + (uint64_t)mst * a_stage;
+          for (int hh = 0; hh < nh; ++hh) {
+            const uint32_t d = tbase + (uint32_t)(hh * 4 * BP) + set;
+            const uint64_t ahi = ast + (uint64_t)hh * a_half;
+            mma_tf32(d, ahi, bdesc, idesc2, kc >= 2 ? 1u : 0u);  // [A_hi v_hi | A_hi v_lo]
+            mma_tf32(d, ahi + a_lo, bdesc, idesc2, 1u);          // + [A_lo v_hi | A_lo v_lo]
+          }
+          mma_commit(&empty[mst]);
+          bdesc += (uint64_t)((2 * kLBO_B) >> 4);
+          if (++mst == NS) { mst = 0; ++muse; }
+        }
+        if (ok) {
+          mma_commit(dfull);
+        } else {
+          *fail = 1;
+          mbar_arrive(dfull);  // release the epilogue threads
+        }
+      }
+      __syncwarp();
+      // ---- epilogue ---------------------------------------------------------------------------
+      // one thread polls the accumulator barrier; the others wait on the named hardware barrier so
+      // that no shared-memory polling competes with the tensor core's operand reads
+      bool okd = true;
+      if (tid == 32) okd = mbar_spin_bounded(dfull, (unsigned)(s & 1), p.status, XBAR_WAIT_LIMIT_NS, 64);
+      if (!okd) atomicExch(fail, 1u);
+      if (epi_sync_or(*fail != 0)) break;
+      fence_after();
+
+      const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
+      const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
+                            : 0.0f;
+      const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
+      const bool have_w = !fwd || s == N - 1;
+      float dots[2];
+      for (int blk = 0; blk < ncb; ++blk) {
+        float a[32];
+        {
+          float a2[32];
+          const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 4 * BP + cb + blk * 32);
+          tmem_ld32(t0, a);
+#pragma unroll
+          for (int part = 1; part < 4; ++part) {  // (even K, v_lo), (odd K, v_hi), (odd K, v_lo)
+            tmem_ld32(t0 + (uint32_t)part * BP, a2);
+#pragma unroll
+            for (int n = 0; n < 32; ++n) a[n] += a2[n];
+          }
+        }
+        const size_t o = rowoff + blk * 32;
+        if (fwd) {
+          if (real)
+            for (int n = 0; n < 32; n += 4)
+              *reinterpret_cast<float4*>(p.z + o + n) = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
+        } else if (real) {
+          for (int n = 0; n < 32; n += 4) {
+            const float4 zz = *reinterpret_cast<const float4*>(p.z + o + n);
+            a[n] += zz.x;
+            a[n + 1] += zz.y;
+            a[n + 2] += zz.z;
+            a[n + 3] += zz.w;
+          }
+        }
+        if (have_w && p.w && real)
+          for (int n = 0; n < 32; n += 4)
+            *reinterpret_cast<float4*>(p.w + o + n) = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
+        if (s + 1 < nsteps) {  // next step's input, split into hi/lo
+          if (nfwd && p.rhs && real) {
+            const float* rn = p.rhs + o + (size_t)Mp * Bpad;
+            for (int n = 0; n < 32; n += 4) {
+              const float4 r4 = *reinterpret_cast<const float4*>(rn + n);
+              put_v(cb + blk * 32 + n, fmaf(ej, a[n], r4.x));
+              put_v(cb + blk * 32 + n + 1, fmaf(ej, a[n + 1], r4.y));
+              put_v(cb + blk * 32 + n + 2, fmaf(ej, a[n + 2], r4.z));
+              put_v(cb + blk * 32 + n + 3, fmaf(ej, a[n + 3], r4.w));
+            }
+          } else {
+            for (int n = 0; n < 32; ++n) put_v(cb + blk * 32 + n, ej * a[n]);
+          }
+        }
+        if (have_w) {
+          for (int n = 0; n < 32; ++n) a[n] *= hj;
+          dots[blk] = transpose_sum32(a, lane);
+        }
+      }
+      if (have_w)
+        for (int blk = 0; blk < ncb; ++blk) red[warp * 64 + cb + blk * 32 + lane] = dots[blk];
+      fence_proxy_async_smem();
+      fence_before();
+      epi_sync();
+      if (have_w && tid < BP) {
+        float sum = 0.0f;
+        if (nh == 2) {
+          for (int w = 0; w < 8; ++w) sum += red[w * 64 + tid];
+        } else {
+          const int s0 = (tid >> 5) * 4;  // warps covering this column block
+          for (int w = s0; w < s0 + 4; ++w) sum += red[w * 64 + tid];
+        }
+        const int b = b0 + tid;
+        if (b < p.B) {
+          double* Ip = p.I + (size_t)b * N + j;
+          const double dI = (double)sum;
+          if (!isfinite(dI)) set_status(p.status, XBAR_DEV_NONFINITE);
+          if (p.accumulate) {
+            const double In = *Ip + dI;
+            *Ip = In;
+            local_max = fmaxf(local_max, (float)(fabs(dI) / fmax(fabs(In), 1e-300)));
+          } else {
+            *Ip = dI;
+          }
+        }
+      }
+    }
+    if (p.max_rel) {
+      for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+      if (lane == 0 && local_max > 0.0f) atomic_max_nonneg(p.max_rel, local_max);
+    }
+  }
+  // ---- teardown: all 9 warps; free tensor memory ------------------------------------------------
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) tmem_dealloc(tbase, ncols);
+}
+
+size_t sweep_tc_smem_bytes(int Mt) {
+  const int NS = Mt == 128 ? 8 : 5;
+  return 256 + 8 * 64 * 4 + (size_t)NS * (2 * tc::kKC * Mt * 4) + (size_t)(Mt / 4) * tc::kLBO_B;
+}
+
+bool sweep_tc_supported(int Mp) { return Mp <= 256; }
+
+int sweep_tc_rows(int Mp) { return Mp <= 128 ? 128 : 256; }
+
+cudaError_t launch_sweep_tc_tile(const float* X, float* Xt, int Mp, int N, cudaStream_t st) {
+  const int Mt = sweep_tc_rows(Mp);
+  const size_t n = (size_t)Mt * Mt * N;
+  sweep_tc_tile_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, Xt, Mp, Mt, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaStream_t st) {
+  const int Mt = sweep_tc_rows(p.Mp);
+  if (p.Bp != tc::kBP || p.Bpad % tc::kBP) return cudaErrorInvalidValue;
+  const int blocks = (p.B + tc::kBP - 1) / tc::kBP;
+  if (blocks == 0) return cudaSuccess;
+  const size_t smem = sweep_tc_smem_bytes(Mt);
+  cudaError_t err = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  sweep_tc_kernel<<<blocks, tc::kThreads + 32, smem, st>>>(p, Xt, Mt);
+  return cudaGetLastError();
+}
+
+}  // namespace xbar
