@@ -132,6 +132,16 @@ xbar_status xbar_factor(xbar_t h, xbar_precision p);
 xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, double* vWL, double* vBL,
                        double tol, int max_iter, xbar_solve_info* info);
 
+/* Kernel-variant options of a handle (value -1 = automatic choice). */
+typedef enum {
+  XBAR_OPT_SWEEP_KERNEL = 0,  /* FP32 substitutions: 0 = CUDA-core kernel, 1 = tensor-core kernel */
+  XBAR_OPT_FACTOR_KERNEL = 1  /* FP32 factor: 0 = cooperative-group kernel, 1 = cluster kernel */
+} xbar_option;
+
+/* Select a kernel variant for later xbar_factor / xbar_solve calls; a variant that does not
+ * support the handle's size falls back to the other.  Errors: XBAR_EINVAL. */
+xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value);
+
 /*
  * xbar_set_conductances -- re-assemble the handle for a new conductance map G
  * (same M, N and resistances; host or device pointer, validated as in
@@ -185,6 +195,55 @@ xbar_status xbar_profile_read(xbar_t h, xbar_profile* out, int reset);
  * pointers, B < 0, scratch too large), XBAR_ECUDA.
  */
 xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batches of tiles: many crossbars of uneven sizes, such as the tiles a network layer is mapped
+ * onto or the parts of a large crossbar split as in Sec. III-C ("Partitioning"), factored and
+ * solved with their input batches by one CUDA-graph launch.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+  int M, N;           /* tile size (word lines, bit lines), as in xbar_assemble */
+  const double* G;    /* M x N conductances (host or device; copied) */
+  double R_s, R_w, R_b, R_sense;
+} xbar_tile;
+
+/* Assemble T tiles; each tile gets its own stream.  Runs start after the work already queued on
+ * `cuda_stream` (NULL = legacy default stream) and return when finished.
+ * Errors: as xbar_assemble, for the first failing tile. */
+xbar_status xbar_batch_create(int T, const xbar_tile* tiles, void* cuda_stream, xbar_batch_t* out);
+
+/*
+ * xbar_batch_run -- factor every tile with precision p (Sec. II-C: one decomposition per map)
+ * and substitute its batch (Sec. III-A), all as one CUDA-graph launch.
+ *   B[t]       input vectors of tile t (>= 0)
+ *   V[t]       B[t] x M_t input voltages, DEVICE memory
+ *   I[t]       B[t] x N_t bit-line currents (output), DEVICE memory
+ *   tol, max_iter   as xbar_solve; refinement runs exactly max_iter passes per tile, and the
+ *              passes after a tile has converged (same stopping rule as xbar_solve) skip their
+ *              work on the device.
+ *   infos      optional, T entries.
+ * The first run with a given (p, B, V, I, tol, max_iter) executes once eagerly (sizing every
+ * workspace) and captures the graph; later runs with the same signature replay it.  Returns
+ * after the graph has completed.  Errors: XBAR_EINVAL (NULL or host pointers, B < 0, bad
+ * precision), XBAR_ENOTCONV (some tile did not converge; infos say which), XBAR_ETIMEOUT,
+ * XBAR_ECUDA, XBAR_ENOMEM.
+ */
+xbar_status xbar_batch_run(xbar_batch_t b, xbar_precision p, const int* B, const double* const* V,
+                           double* const* I, double tol, int max_iter, xbar_solve_info* infos);
+
+/*
+ * xbar_batch_autotune -- for every distinct (M, N, B[t]) time the kernel variants (tensor-core
+ * vs CUDA-core FP32 substitutions, cluster vs cooperative-group FP32 factor) on one tile, keep
+ * the fastest for all tiles of that shape.  cache_path (may be NULL) is a JSON file of earlier
+ * choices, read first and rewritten with new ones.  Only XBAR_FP32_IR has variants.
+ */
+xbar_status xbar_batch_autotune(xbar_batch_t b, xbar_precision p, const int* B, const char* cache_path);
+
+/* The handle of tile t (owned by the batch: do not destroy it). */
+xbar_status xbar_batch_tile(xbar_batch_t b, int t, xbar_t* out);
+
+/* Release the batch, its tiles, streams and graph.  NULL is accepted. */
+xbar_status xbar_batch_destroy(xbar_batch_t b);
 
 /* Wait for the handle's stream and report any device-recorded error. */
 xbar_status xbar_sync(xbar_t h);

@@ -12,6 +12,7 @@
 
 #include "xbar.h"
 #include "common.cuh"
+#include "handle.h"
 #include "kernels.h"
 
 using namespace xbar;
@@ -28,6 +29,16 @@ static xbar_status fail(xbar_status s, const char* fmt, ...) {
   return s;
 }
 
+xbar_status xbar::set_error(xbar_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
 #define XB_CUDA(call)                                                                      \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \
@@ -39,117 +50,6 @@ static xbar_status fail(xbar_status s, const char* fmt, ...) {
       return fail(XBAR_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     }                                                                                      \
   } while (0)
-
-namespace {
-
-// device allocation owned by a handle; freed in reverse order on destroy
-struct DevArena {
-  std::vector<void*> ptrs;
-  cudaError_t alloc(void** p, size_t bytes) {
-    *p = nullptr;
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e == cudaSuccess) ptrs.push_back(*p);
-    return e;
-  }
-  void release(void* p) {
-    for (size_t k = 0; k < ptrs.size(); ++k)
-      if (ptrs[k] == p) {
-        cudaFree(p);
-        ptrs.erase(ptrs.begin() + k);
-        return;
-      }
-  }
-  void free_all() {
-    for (size_t k = ptrs.size(); k-- > 0;) cudaFree(ptrs[k]);
-    ptrs.clear();
-  }
-};
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// growable device buffer
-struct Buf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-cudaError_t ensure(DevArena& A, Buf& b, size_t bytes) {
-  if (b.bytes >= bytes && b.p) return cudaSuccess;
-  if (b.p) A.release(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
-  cudaError_t e = A.alloc(&b.p, bytes);
-  if (e == cudaSuccess) b.bytes = bytes;
-  return e;
-}
-
-int round_up(int a, int m) { return ((a + m - 1) / m) * m; }
-
-}  // namespace
-
-struct xbar_s {
-  MapDev m;
-  double R[4] = {0, 0, 0, 0};
-  cudaStream_t st = nullptr;
-  int dev = 0, nsm = 0;
-  int factored = 0;
-  xbar_precision prec = XBAR_FP64;
-  DevArena A;
-  unsigned* status = nullptr;
-  // factor
-  Buf X, fsig, fpbuf, fbar, fparams;
-  Buf Xt;          // tensor-core tiled TF32 hi/lo copy of the FP32 factor
-  int tc_ready = 0;
-  // solve workspace
-  Buf z, dhat, rhat, w64, phi, maxrel, rmax;
-  // staging for host pointers
-  Buf sV, sI, svWL, svBL;
-  // profiling: events recorded around launches, resolved in xbar_profile_read
-  int prof_on = 0;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
-  xbar_profile prof;
-};
-
-// RAII scope that brackets the launches of one phase with events when profiling is on
-struct PhaseScope {
-  xbar_s* h;
-  int phase;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int nlaunch;
-  PhaseScope(xbar_s* h_, int ph, int n = 1) : h(h_), phase(ph), nlaunch(n) {
-    if (!h->prof_on) return;
-    e0 = take();
-    e1 = take();
-    if (e0) cudaEventRecord(e0, h->st);
-  }
-  cudaEvent_t take() {
-    if (!h->ev_pool.empty()) {
-      cudaEvent_t e = h->ev_pool.back();
-      h->ev_pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    return e;
-  }
-  ~PhaseScope() {
-    if (!h->prof_on || !e0 || !e1) return;
-    cudaEventRecord(e1, h->st);
-    h->pending.push_back({phase, {e0, e1}});
-    h->prof.launches[phase] += nlaunch;
-  }
-};
 
 static const char* kVersion = "libxbar 0.1 (sm_103a)";
 
@@ -257,24 +157,28 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   return XBAR_OK;
 }
 
-// FP32 substitutions run on the tensor cores (sweep_tc.cu) when the block fits (Mp <= 256);
-// XBAR_SWEEP=simt in the environment selects the CUDA-core kernel instead.
-static bool use_tc_sweep(int Mp) {
+// Kernel variants.  FP32 substitutions run on the tensor cores (sweep_tc.cu) when the block fits
+// (Mp <= 256) and FP32 factors on a thread-block cluster (factor_cluster.cu) when 32 <= Mp <= 256,
+// unless the handle's options (xbar_set_option, set by the batch autotuner) or the environment
+// (XBAR_SWEEP=simt|tc, XBAR_FACTOR=group|cluster) choose otherwise.
+bool xbar::use_tc_sweep(const xbar_s* h) {
+  if (!sweep_tc_supported(h->m.Mp)) return false;
   const char* e = getenv("XBAR_SWEEP");
   if (e && strcmp(e, "simt") == 0) return false;
-  return sweep_tc_supported(Mp);
+  if (e && strcmp(e, "tc") == 0) return true;
+  return h->opt.sweep != 0;
 }
 
-// FP32 factors run on a thread-block cluster (factor_cluster.cu) when 32 <= Mp <= 256;
-// XBAR_FACTOR=group in the environment selects the cooperative-group kernel instead.
-static bool use_cluster_factor(int Mp) {
+bool xbar::use_cluster_factor(const xbar_s* h) {
+  if (!factor_cluster_supported(h->m.Mp)) return false;
   const char* e = getenv("XBAR_FACTOR");
   if (e && strcmp(e, "group") == 0) return false;
-  return factor_cluster_supported(Mp);
+  if (e && strcmp(e, "cluster") == 0) return true;
+  return h->opt.factor != 0;
 }
 
 template <typename T>
-static xbar_status do_factor(xbar_t h, bool equilibrate) {
+static xbar_status do_factor(xbar_t h, bool equilibrate, bool upload) {
   MapDev& m = h->m;
   const int Mp = m.Mp, N = m.N;
   const int PB = factor_panel_width<T>();
@@ -304,14 +208,17 @@ static xbar_status do_factor(xbar_t h, bool equilibrate) {
   fp.pbuf = (T*)h->fpbuf.p;
   fp.bar = (unsigned*)h->fbar.p;
   XB_CUDA(cudaMemsetAsync(h->fbar.p, 0, 2 * sizeof(unsigned), h->st));
-  XB_CUDA(cudaMemcpyAsync(h->fparams.p, &fp, sizeof(fp), cudaMemcpyHostToDevice, h->st));
-  PhaseScope ps(h, XBAR_PHASE_FACTOR, sizeof(T) == 4 && use_tc_sweep(Mp) ? 2 : 1);
-  if (sizeof(T) == 4 && use_cluster_factor(Mp))
+  if (upload) {
+    XB_CUDA(cudaMemcpyAsync(h->fparams.p, &fp, sizeof(fp), cudaMemcpyHostToDevice, h->st));
+    XB_CUDA(cudaStreamSynchronize(h->st));  // fp is a stack variable
+  }
+  PhaseScope ps(h, XBAR_PHASE_FACTOR, sizeof(T) == 4 && use_tc_sweep(h) ? 2 : 1);
+  if (sizeof(T) == 4 && use_cluster_factor(h))
     XB_CUDA(launch_factor_cluster((const FactorParams<float>*)h->fparams.p, 1, Mp, h->status, h->st));
   else
     XB_CUDA(launch_factor<T>((const FactorParams<T>*)h->fparams.p, 1, Mp, bpm, h->status, h->st));
   h->tc_ready = 0;
-  if (sizeof(T) == 4 && use_tc_sweep(Mp)) {
+  if (sizeof(T) == 4 && use_tc_sweep(h)) {
     const int Mt = sweep_tc_rows(Mp);
     XB_CUDA(ensure(h->A, h->Xt, (size_t)N * Mt * Mt * 2 * sizeof(float)));
     XB_CUDA(launch_sweep_tc_tile((const float*)h->X.p, (float*)h->Xt.p, Mp, N, h->st));
@@ -320,15 +227,31 @@ static xbar_status do_factor(xbar_t h, bool equilibrate) {
   return XBAR_OK;
 }
 
+xbar_status xbar::factor_handle(xbar_s* h, xbar_precision p, bool upload_params) {
+  h->factored = 0;
+  xbar_status s = (p == XBAR_FP64) ? do_factor<double>(h, false, upload_params)
+                                   : do_factor<float>(h, true, upload_params);
+  if (s != XBAR_OK) return s;
+  h->prec = p;
+  h->factored = 1;
+  return XBAR_OK;
+}
+
 extern "C" xbar_status xbar_factor(xbar_t h, xbar_precision p) {
   if (!h) return fail(XBAR_EINVAL, "handle is NULL");
   if (p != XBAR_FP64 && p != XBAR_FP32_IR) return fail(XBAR_EINVAL, "unknown precision %d", (int)p);
   XB_CUDA(cudaSetDevice(h->dev));
-  h->factored = 0;
-  xbar_status s = (p == XBAR_FP64) ? do_factor<double>(h, false) : do_factor<float>(h, true);
-  if (s != XBAR_OK) return s;
-  h->prec = p;
-  h->factored = 1;
+  return factor_handle(h, p, true);
+}
+
+extern "C" xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (value < -1 || value > 1) return fail(XBAR_EINVAL, "option value %d outside [-1, 1]", value);
+  switch (opt) {
+    case XBAR_OPT_SWEEP_KERNEL: h->opt.sweep = value; break;
+    case XBAR_OPT_FACTOR_KERNEL: h->opt.factor = value; break;
+    default: return fail(XBAR_EINVAL, "unknown option %d", (int)opt);
+  }
   return XBAR_OK;
 }
 
@@ -559,6 +482,70 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
   if (mixed && !converged)
     return fail(XBAR_ENOTCONV, "refinement stopped after %d corrections with max |dI|/|I| = %g > tol = %g",
                 iters, last, tol);
+  return XBAR_OK;
+}
+
+xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double* dI, double tol, int max_iter,
+                                      bool allow_alloc) {
+  MapDev& m = h->m;
+  const int M = m.M, Mp = m.Mp, N = m.N;
+  cudaStream_t st = h->st;
+  const bool mixed = h->prec == XBAR_FP32_IR;
+  const bool tc = mixed && h->tc_ready;
+  const int Bp = tc ? kSweepTcPanel
+                    : (mixed ? sweep_panel_width<float>(Mp, B, h->nsm) : sweep_panel_width<double>(Mp, B, h->nsm));
+  const int Bpad = ((B + Bp - 1) / Bp) * Bp;
+  const size_t nst = (size_t)N * Mp * Bpad;
+  auto need = [&](Buf& b, size_t bytes) -> bool {
+    if (b.p && b.bytes >= bytes) return true;
+    return allow_alloc && ensure(h->A, b, bytes) == cudaSuccess;
+  };
+  if (!need(h->irstate, sizeof(IrState))) return fail(XBAR_ENOMEM, "refinement state");
+  IrState* state = (IrState*)h->irstate.p;
+  if (!mixed) {
+    if (!need(h->z, nst * 8)) return fail(XBAR_ENOMEM, "workspace not prepared for this batch size");
+    SweepParams<double> sp;
+    sp.M = M; sp.Mp = Mp; sp.N = N; sp.B = B; sp.Bp = Bp; sp.Bpad = Bpad;
+    sp.X = (const double*)h->X.p; sp.e = m.e_pl; sp.hs = m.h; sp.src = m.src_pl;
+    sp.V = dV; sp.rhs = nullptr; sp.z = (double*)h->z.p; sp.w = nullptr; sp.I = dI;
+    sp.accumulate = 0; sp.max_rel = nullptr; sp.status = h->status;
+    XB_CUDA(launch_ir_init(state, st));
+    XB_CUDA(launch_sweep<double>(sp, st));
+    return XBAR_OK;
+  }
+  if (!need(h->z, nst * 4) || !need(h->dhat, nst * 4) || !need(h->rhat, nst * 4) || !need(h->w64, nst * 8) ||
+      !need(h->phi, nst * 8))
+    return fail(XBAR_ENOMEM, "workspace not prepared for this batch size");
+  ResidParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.M = M; rp.Mp = Mp; rp.N = N; rp.B = B; rp.Bpad = Bpad;
+  rp.gs = m.gs; rp.gw = m.gw; rp.Gc = m.Gc; rp.dW = m.dW; rp.h = m.h; rp.tha = m.tha; rp.thc = m.thc;
+  rp.s32 = m.s32; rp.V = dV; rp.I = dI; rp.status = h->status;
+  rp.w = (double*)h->w64.p; rp.dhat = (const float*)h->dhat.p; rp.phi = (double*)h->phi.p;
+  rp.rhat = (float*)h->rhat.p; rp.rmax = &state->rmax;
+  SweepParams<float> sp;
+  sp.M = M; sp.Mp = Mp; sp.N = N; sp.B = B; sp.Bp = Bp; sp.Bpad = Bpad;
+  sp.X = (const float*)h->X.p; sp.e = m.e32; sp.hs = m.hs32; sp.src = m.src32;
+  sp.V = dV; sp.rhs = nullptr; sp.z = (float*)h->z.p; sp.w = (float*)h->dhat.p; sp.I = dI;
+  sp.accumulate = 0; sp.max_rel = nullptr; sp.status = h->status;
+  auto sweep = [&]() -> cudaError_t {
+    return tc ? launch_sweep_tc(sp, (const float*)h->Xt.p, st) : launch_sweep<float>(sp, st);
+  };
+  XB_CUDA(launch_ir_init(state, st));
+  XB_CUDA(sweep());                      // x0 = solve32(b)
+  XB_CUDA(launch_update(rp, 1, st));     // w = s o dhat, I = h . w
+  sp.V = nullptr;
+  sp.rhs = (const float*)h->rhat.p;
+  sp.accumulate = 1;
+  sp.max_rel = &state->maxrel;
+  sp.skip = &state->done;
+  rp.skip = &state->done;
+  for (int it = 0; it < max_iter; ++it) {
+    XB_CUDA(launch_resid(rp, st));       // rhat = s o (b - A w)   [FP64]  (skipped once converged)
+    XB_CUDA(sweep());                    // dhat = solve32(rhat), I += dI
+    XB_CUDA(launch_ir_check(state, tol, st));
+    XB_CUDA(launch_update(rp, 0, st));   // w += s o dhat, I = h . w   (skipped once converged)
+  }
   return XBAR_OK;
 }
 

@@ -253,7 +253,7 @@ cudaError_t launch_factor(const FactorParams<T>* maps_dev, int nmaps, int Mp_max
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = (nmaps * blocks_per_map > 1) ? 1 : 0;  // one block needs no co-residency guarantee
   return cudaLaunchKernelEx(&cfg, factor_kernel<T>, maps_dev, blocks_per_map, status);
 }
 

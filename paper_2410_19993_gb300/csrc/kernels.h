@@ -84,6 +84,7 @@ struct SweepParams {
   int accumulate;      // 0: I = dI   1: I += dI
   float* max_rel;      // atomic max of |dI| / |I| (accumulate mode), or nullptr
   unsigned* status;
+  const int* skip = nullptr;  // if set and nonzero at launch, the kernel does nothing
 };
 
 template <typename T>
@@ -117,6 +118,7 @@ struct ResidParams {
   double* I;            // [B][N]
   unsigned long long* rmax;  // bit pattern of max |r| (non-negative double)
   unsigned* status;
+  const int* skip;           // if set and nonzero at launch, the kernel does nothing
 };
 // w = (first ? 0 : w) + s * dhat ; I = h . w
 cudaError_t launch_update(const ResidParams& p, int first, cudaStream_t st);
@@ -127,6 +129,12 @@ cudaError_t launch_blvolt(const ResidParams& p, double* u, cudaStream_t st);
 // out[b][i][j] = src[(j*Mp + i)*Bpad + b]
 cudaError_t launch_to_user_layout(const double* src, double* out, int M, int Mp, int N, int B, int Bpad,
                                   cudaStream_t st);
+// device-driven refinement control (one thread): reset the state / apply the stopping rule to the
+// correction just computed (state->maxrel, state->rmax), set state->done, and re-arm the
+// accumulators for the next pass
+struct IrState;
+cudaError_t launch_ir_init(IrState* state, cudaStream_t st);
+cudaError_t launch_ir_check(IrState* state, double tol, cudaStream_t st);
 // FP64 -> FP32 copy
 cudaError_t launch_d2f(const double* a, float* b, size_t n, cudaStream_t st);
 

@@ -15,12 +15,14 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "handle.h"
 #include "kernels.h"
 
 namespace xbar {
 
 // w = (first ? 0 : w) + s * dhat  (FP64),  I[b][j] = h_j . w_j  (FP64)
 __global__ void update_kernel(ResidParams p, int first) {
+  if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (b >= p.Bpad || j >= p.N) return;
@@ -48,6 +50,7 @@ __device__ __forceinline__ void chain_forward(const ResidParams& p, int j, int b
 }
 
 __global__ void resid_kernel(ResidParams p) {
+  if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (b >= p.Bpad || j >= p.N) return;
@@ -111,6 +114,41 @@ cudaError_t launch_resid(const ResidParams& p, cudaStream_t st) {
 cudaError_t launch_blvolt(const ResidParams& p, double* u, cudaStream_t st) {
   dim3 grid((p.Bpad + 127) / 128, p.N);
   blvolt_kernel<<<grid, 128, 0, st>>>(p, u);
+  return cudaGetLastError();
+}
+
+__global__ void ir_init_kernel(IrState* s) {
+  s->done = 0;
+  s->iters = 0;
+  s->last = 0.0f;
+  s->prev = 0.0f;
+  s->maxrel = 0.0f;
+  s->rmax = 0ull;
+  s->rinf = 0.0;
+}
+
+// the stopping rule of the host-driven loop: converged when this correction is within tol, or when
+// the observed contraction rho = |dI_k| / |dI_{k-1}| (<= 1/2) bounds the error left after it
+__global__ void ir_check_kernel(IrState* s, double tol) {
+  if (s->done) return;
+  const float mr = s->maxrel;
+  s->prev = s->last;
+  s->last = mr;
+  s->iters += 1;
+  s->rinf = __longlong_as_double((long long)s->rmax);
+  const double rho = (s->iters >= 2 && s->prev > 0.0f) ? (double)mr / s->prev : 1.0;
+  if (mr == mr && (mr <= tol || (rho <= 0.5 && (double)mr * rho / (1.0 - rho) <= tol))) s->done = 1;
+  s->maxrel = 0.0f;
+  s->rmax = 0ull;
+}
+
+cudaError_t launch_ir_init(IrState* state, cudaStream_t st) {
+  ir_init_kernel<<<1, 1, 0, st>>>(state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_check(IrState* state, double tol, cudaStream_t st) {
+  ir_check_kernel<<<1, 1, 0, st>>>(state, tol);
   return cudaGetLastError();
 }
 

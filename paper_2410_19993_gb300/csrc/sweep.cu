@@ -86,6 +86,7 @@ __global__ void sweep_kernel(SweepParams<T> p, int KC) {
   T* vin = xs + 2 * (size_t)KC * Mp;                                       // [Mp][Bp]
   T* red = vin + (size_t)Mp * Bp;                                          // [nrg][Bp]
 
+  if (p.skip && *p.skip) return;
   if (nrg * ncg != (int)blockDim.x || b0 + Bp > Bpad) {
     if (tid == 0) set_status(p.status, XBAR_DEV_BADLAUNCH);
     return;

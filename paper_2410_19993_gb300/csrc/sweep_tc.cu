@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
   const uint32_t idesc2 = idesc_tf32(128, 2 * BP);
   const uint32_t LBO_A = (uint32_t)Mt * 16, SBO = 128;
 
+  if (p.skip && *p.skip) return;  // uniform: before any barrier or tensor-memory allocation
   if ((int)blockDim.x != kThreads + 32 || (nh != 1 && nh != 2) || b0 + BP > Bpad) {
     if (tid == 0) set_status(p.status, XBAR_DEV_BADLAUNCH);
     return;

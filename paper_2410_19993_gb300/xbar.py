@@ -46,6 +46,13 @@ class Profile(ctypes.Structure):
         return {ph: {"launches": int(self.launches[k]), "ms": float(self.ms[k])} for k, ph in enumerate(PHASES)}
 
 
+class TileDesc(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("G", ctypes.c_void_p), ("R_s", ctypes.c_double),
+                ("R_w", ctypes.c_double), ("R_b", ctypes.c_double), ("R_sense", ctypes.c_double)]
+
+
+OPTIONS = {"sweep_kernel": 0, "factor_kernel": 1}
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -73,13 +80,22 @@ def load(build_if_missing: bool = True):
     lib.xbar_sync.argtypes = [_vp]
     lib.xbar_set_conductances.argtypes = [_vp, _vp]
     lib.xbar_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    lib.xbar_set_option.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    lib.xbar_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(TileDesc), _vp, ctypes.POINTER(_vp)]
+    lib.xbar_batch_run.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int, ctypes.POINTER(SolveInfo)]
+    lib.xbar_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p]
+    lib.xbar_batch_tile.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(_vp)]
+    lib.xbar_batch_destroy.argtypes = [_vp]
     lib.xbar_profile_enable.argtypes = [_vp, ctypes.c_int]
     lib.xbar_profile_read.argtypes = [_vp, ctypes.POINTER(Profile), ctypes.c_int]
     lib.xbar_destroy.argtypes = [_vp]
     lib.xbar_last_error.restype = ctypes.c_char_p
     lib.xbar_version.restype = ctypes.c_char_p
     for f in ("xbar_assemble", "xbar_factor", "xbar_solve", "xbar_sync", "xbar_destroy", "xbar_set_conductances",
-              "xbar_profile_enable", "xbar_profile_read", "xbar_solve_noalloc"):
+              "xbar_profile_enable", "xbar_profile_read", "xbar_solve_noalloc", "xbar_set_option",
+              "xbar_batch_create", "xbar_batch_run", "xbar_batch_autotune", "xbar_batch_tile",
+              "xbar_batch_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -150,6 +166,11 @@ class Crossbar:
             _check(st)
         return st
 
+    def set_option(self, name, value):
+        """xbar_set_option: 'sweep_kernel' (0 CUDA cores, 1 tensor cores) / 'factor_kernel' (0 group, 1 cluster)."""
+        _check(load().xbar_set_option(self.handle, OPTIONS[name], int(value)))
+        return self
+
     def set_conductances(self, G):
         _check(load().xbar_set_conductances(self.handle, _ptr(G)))
         return self
@@ -168,6 +189,56 @@ class Crossbar:
     def destroy(self):
         if self.handle:
             load().xbar_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Batch:
+    """xbar_batch_*: many tiles factored and solved by one CUDA-graph launch (device buffers only)."""
+
+    def __init__(self, tiles, stream=None):
+        """tiles: list of (G [M x N], R_s, R_w, R_b, R_sense)."""
+        lib = load()
+        self._G = [t[0] for t in tiles]
+        arr = (TileDesc * len(tiles))()
+        for k, (G, Rs, Rw, Rb, Rse) in enumerate(tiles):
+            arr[k] = TileDesc(int(G.shape[0]), int(G.shape[1]), _ptr(G), Rs, Rw, Rb, Rse)
+        h = _vp()
+        _check(lib.xbar_batch_create(len(tiles), arr, _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h.value
+        self.T = len(tiles)
+
+    def autotune(self, precision, B, cache_path=None):
+        Barr = (ctypes.c_int * self.T)(*[int(b) for b in B])
+        _check(load().xbar_batch_autotune(self.handle, PRECISIONS.get(precision, precision), Barr,
+                                          cache_path.encode() if cache_path else None))
+
+    def run(self, precision, Vs, Is, tol=1e-8, max_iter=6, raise_on_error=True):
+        """Vs[t]: B_t x M_t, Is[t]: B_t x N_t (CUDA float64 tensors); returns (status, [info dicts])."""
+        T = self.T
+        Barr = (ctypes.c_int * T)(*[int(v.shape[0]) for v in Vs])
+        Varr = (_vp * T)(*[_ptr(v) for v in Vs])
+        Iarr = (_vp * T)(*[_ptr(i) for i in Is])
+        infos = (SolveInfo * T)()
+        st = load().xbar_batch_run(self.handle, PRECISIONS.get(precision, precision), Barr, Varr, Iarr, tol,
+                                   max_iter, infos)
+        if raise_on_error:
+            _check(st)
+        return st, [infos[k].as_dict() for k in range(T)]
+
+    def tile_handle(self, t):
+        h = _vp()
+        _check(load().xbar_batch_tile(self.handle, t, ctypes.byref(h)))
+        return h.value
+
+    def destroy(self):
+        if self.handle:
+            load().xbar_batch_destroy(self.handle)
             self.handle = 0
 
     def __del__(self):
