@@ -72,7 +72,7 @@ typedef struct {
   double max_rel_dI;  /* max over (b, j) of |dI| / |I| of the last correction */
   double resid_inf;   /* max |r| of the last FP64 residual, in amperes (0 for XBAR_FP64) */
   double err_est;     /* estimated max relative current error of the result */
-  int n_fallback;     /* unused by the exact solver (0); see the batch API */
+  int n_fallback;     /* xbar_surrogate_solve: vectors solved exactly (0 elsewhere) */
 } xbar_solve_info;
 
 /*
@@ -244,6 +244,89 @@ xbar_status xbar_batch_tile(xbar_batch_t b, int t, xbar_t* out);
 
 /* Release the batch, its tiles, streams and graph.  NULL is accepted. */
 xbar_status xbar_batch_destroy(xbar_batch_t b);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned surrogate of the column currents, with the exact solver as fallback and judge.
+ *
+ * The paper's closing section proposes driving whole neural-network simulations with the solver;
+ * at that scale most input vectors need only a close estimate.  Two stages:
+ *   line model: every word line solved alone with the bit lines at ground, then every bit line
+ *     solved alone with its devices driven by those word-line voltages; each further pass
+ *     solves the word lines again with their devices tied to the latest bit-line voltages, then
+ *     the bit lines again (block Gauss-Seidel between the two sets of lines, which converges to
+ *     the exact solution).  Linear in V: I_line = V T_line, T_line found per map from the M unit
+ *     inputs in O(passes M^2 N).  One pass: T_line(i, j) = tau(i, j) G(i, j) g_o x_j(i) with tau
+ *     the word-line voltage ratios and x_j bit line j's response to a unit bottom current.
+ *   network: for bit line j it reads 3M features
+ *     x = [ G(:,j) / g_scale,  V / v_scale,  S(:,j) / (N g_scale) ],  S(i, j) = sum_{l>=j} G(i, l)
+ *     (3M -> 256 -> 256 -> 2, ReLU, BF16 weights and activations, FP32 accumulation) with outputs
+ *     (n0, n1), trained on the line model's error relative to the ideal MVM, standardised:
+ *       q = (I_j - I_line,j) / I_ideal,j,  I_ideal,j = sum_i V_i G_ij,  qh = (q - mu) / sigma;
+ *       n0 ~ qh,   n1 ~ log |n0 - qh|  (the network's own error).
+ * Prediction: I_j = I_line,j + I_ideal,j (mu + sigma n0); its deviation from the ideal MVM is
+ * (I_line,j - I_ideal,j)/I_ideal,j + mu + sigma n0.  Relative error estimate
+ * c sigma exp(n1) |I_ideal,j| / |I_j| with c from calibration.
+ * Training loss per row: (n0 - qh)^2 + 0.1 (n1 - log(|n0 - qh| + 1e-6))^2 (the log target is
+ * held constant), mean over the rows of a minibatch, Adam (beta 0.9 / 0.999, eps 1e-8) on FP32
+ * master weights.  Flat parameter order: W1 [256][Fp] (Fp = 3M rounded up to 128; padding
+ * columns zero), b1 [256], W2 [256][256], b2 [256], W3 [2][256], b3 [2]; W[o][i] maps input i to
+ * output o.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct xbar_surrogate_s* xbar_surrogate_t;
+
+/* Create a surrogate for M x N maps (1 <= M <= 1024) of the circuit (R_s, R_w, R_b, R_sense, as
+ * in xbar_assemble) whose line model runs line_passes passes (1..64), with He-initialised
+ * weights from `seed`.  g_scale, v_scale > 0 normalise conductances and voltages.  Work is queued
+ * on `cuda_stream` (NULL = legacy default stream).  Errors: XBAR_EINVAL, XBAR_ENOMEM, XBAR_ECUDA. */
+xbar_status xbar_surrogate_create(int M, int N, double R_s, double R_w, double R_b, double R_sense,
+                                  int line_passes, double g_scale, double v_scale, unsigned seed,
+                                  void* cuda_stream, xbar_surrogate_t* out);
+
+/* Read (get != NULL) and/or replace (set != NULL) the flat FP32 parameters (host or device);
+ * *count (may be NULL) receives their number.  `set` is applied before `get`. */
+xbar_status xbar_surrogate_params(xbar_surrogate_t s, float* get, const float* set, int* count);
+
+/* Read (get != NULL) and/or replace (set != NULL; applied first) the three scalars around the
+ * network: {mu, sigma, c}.  The target is standardised as (y - mu) / sigma; mu and sigma are set
+ * from the targets of the first xbar_surrogate_train call unless set here first (default 0, 1);
+ * c is the calibrated error-estimate scale (default 1).  Errors: XBAR_EINVAL (sigma or c <= 0). */
+xbar_status xbar_surrogate_scaling(xbar_surrogate_t s, const double* set, double* get);
+
+/* Loss and gradient of one minibatch without updating: X is R x 3M FP32 features (host or
+ * device, row-major), y R raw targets q (standardised inside with mu, sigma).
+ * loss[0] = mean (n0 - qh)^2, loss[1] = mean (n1 - t)^2;
+ * grad (may be NULL) receives the gradient of loss[0] + 0.1 loss[1] in the flat order.  The
+ * network computes in BF16 exactly as in training. */
+xbar_status xbar_surrogate_grad(xbar_surrogate_t s, int R, const float* X, const float* y, double* loss,
+                                float* grad);
+
+/* Train on n_maps maps: G[m] (M x N), V[m] (B[m] x M) and the exact currents I[m] (B[m] x N)
+ * (host or device).  Rows are shuffled in minibatches of batch_rows (a multiple of 128) each
+ * epoch; loss_per_epoch (may be NULL, 2*epochs) receives the two mean losses of each epoch. */
+xbar_status xbar_surrogate_train(xbar_surrogate_t s, int n_maps, const double* const* G, const int* B,
+                                 const double* const* V, const double* const* I, int epochs, int batch_rows,
+                                 double lr, unsigned seed, double* loss_per_epoch);
+
+/* Set the error-estimate scale c so that the given quantile (0 < q <= 1) of |I_pred - I| / |I|
+ * over held-out maps lies at or below c exp(out1).  *scale_out (may be NULL) receives c. */
+xbar_status xbar_surrogate_calibrate(xbar_surrogate_t s, int n_maps, const double* const* G, const int* B,
+                                     const double* const* V, const double* const* I, double quantile,
+                                     double* scale_out);
+
+/* Predict the B x N currents of map G for inputs V (B x M); err_est (may be NULL) receives the
+ * relative error estimates.  Host or device pointers; returns when the results are written. */
+xbar_status xbar_surrogate_predict(xbar_surrogate_t s, const double* G, int B, const double* V, double* I,
+                                   double* err_est);
+
+/* Predict for the map held by `exact` (an assembled handle of the same M, N and circuit) and replace every
+ * input vector with an error estimate above `bound` by the exact solution (xbar_solve with
+ * XBAR_FP32_IR, tol 1e-8; the handle is factored on first need).  V, I, err_est: DEVICE memory.
+ * info->n_fallback counts the vectors solved exactly; the other fields describe that solve. */
+xbar_status xbar_surrogate_solve(xbar_surrogate_t s, xbar_t exact, int B, const double* V, double* I,
+                                 double bound, double* err_est, xbar_solve_info* info);
+
+/* Release the surrogate.  NULL is accepted. */
+xbar_status xbar_surrogate_destroy(xbar_surrogate_t s);
 
 /* Wait for the handle's stream and report any device-recorded error. */
 xbar_status xbar_sync(xbar_t h);

@@ -6,6 +6,7 @@
 //   batch vectors        [N][Mp][Bpad]  column j, row i, input vector b at (j*Mp + i)*Bpad + b
 //   user inputs          V[B][M], I[B][N], node voltages [B][M][N]
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -99,6 +100,28 @@ constexpr int kSweepTcPanel = 64;
 // X (FP32 [N][Mp][Mp]) -> Xt: TF32 hi/lo split in the MMA's chunked core-matrix order
 cudaError_t launch_sweep_tc_tile(const float* X, float* Xt, int Mp, int N, cudaStream_t st);
 cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaStream_t st);
+
+// ---- BF16 tensor-core GEMM (gemm_bf16.cu): C[m][n] = sum_k A(m,k) B(n,k) ---------------------
+enum { GEMM_EPI_STORE = 0, GEMM_EPI_BIAS_RELU = 1, GEMM_EPI_MASK = 2 };
+struct GemmBf16Params {
+  int M, N, K;                          // multiples of 128, 128, 64
+  const struct __nv_bfloat16* A;        // A(m,k) = A[m*sAm + k*sAk]   (sAk == 1 or sAm == 1)
+  long sAm, sAk;
+  const struct __nv_bfloat16* B;        // B(n,k) = B[n*sBn + k*sBk]   (sBk == 1 or sBn == 1)
+  long sBn, sBk;
+  int mode;                             // GEMM_EPI_*
+  float* C;                             // EPI_STORE: C[m*ldc + n] (= or atomically +=)
+  long ldc;
+  int atomic;
+  const float* bias;                    // EPI_BIAS_RELU: out = relu(C + bias[n])
+  const struct __nv_bfloat16* mask;     // EPI_MASK: out = mask > 0 ? C : 0
+  long ldm;
+  struct __nv_bfloat16* out;            // BF16 output of EPI_BIAS_RELU / EPI_MASK
+  long ldo;
+  unsigned* status;
+};
+// ksplit > 1 splits K over blocks and requires EPI_STORE with atomic = 1 (C zeroed by the caller)
+cudaError_t launch_gemm_bf16(const GemmBf16Params& p, int ksplit, cudaStream_t st);
 
 // ---- FP64 refinement kernels and node voltages ------------------------------------------------
 struct ResidParams {

@@ -1,0 +1,903 @@
+// surrogate.cu -- a learned per-column surrogate of the crossbar solve, trained on solves the
+// exact method produces, with the exact solver as its fallback.
+//
+// Line model (a cheap physical estimate the network corrects): every word line is solved alone
+// with the bit lines at ground, giving word-line voltage ratios tau(i, j); then every bit line is
+// solved alone with device i driven by V_i tau(i, j).  It is linear in V:
+//     I_line = V T_line,   T_line(i, j) = tau(i, j) G(i, j) g_o x_j(i),
+// x_j solving bit line j's chain for a unit current at its bottom node.  Both chains are walked
+// once from their open end with subtraction-free ratio recurrences (one thread per line, FP64).
+//
+// Network: for bit line j of map G and input vector V it reads 3M features
+//     x = [ G(:,j) / g_scale,  V / v_scale,  S(:,j) / (N g_scale) ],  S(i, j) = sum_{l>=j} G(i, l)
+// (S(:,j): the load each word line still carries at column j), 3M -> 256 -> 256 -> 2 with ReLU,
+// BF16 weights and activations in the tensor-core products (gemm_bf16.cu), FP32 accumulation,
+// FP32 master weights and Adam.  Its target is the line model's error relative to the ideal MVM,
+//     q = (I - I_line) / I_ideal,   I_ideal(j) = sum_i V_i G(i, j),
+// standardised as qh = (q - mu) / sigma with mu, sigma from the first training set.  Loss per row:
+//     (n0 - qh)^2 + lambda (n1 - log(|n0 - qh| + 1e-6))^2     (the log target is held constant),
+// averaged over the rows of a minibatch.
+//
+// Prediction: I = I_line + I_ideal (mu + sigma n0), with the relative error estimate
+// c sigma exp(n1) |I_ideal| / |I|, where c is calibrated on held-out solves so that a chosen
+// quantile of the true relative errors lies below the estimate.  xbar_surrogate_solve replaces
+// every vector with an estimate above the bound by the exact solve (factored only when needed).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <random>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+#include "kernels.h"
+
+using namespace xbar;
+
+#define XB_CUDA(call)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      if (e_ == cudaErrorMemoryAllocation) {                                                        \
+        cudaGetLastError();                                                                         \
+        return set_error(XBAR_ENOMEM, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      }                                                                                             \
+      return set_error(XBAR_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                               \
+  } while (0)
+
+namespace {
+
+constexpr int kH = 256;          // hidden width
+constexpr float kLambda = 0.1f;  // weight of the error head
+constexpr float kEps = 1e-6f;    // floor of the error-head target |out0 - y|
+
+// ---- kernels ------------------------------------------------------------------------------------
+
+// ---- line model ---------------------------------------------------------------------------------
+// Every chain is factored once per map by elimination from its far end, which needs only the
+// reciprocal pivots (all other multipliers are g_w or g_b times them):
+//   word line i (nodes j, source g_s at j = 0, far end open), eliminated from j = N-1 down:
+//     D_j = (j == 0 ? g_s : g_w) + G(i, j) + g_w delta_j,  delta_{N-1} = 0,
+//     delta_{j-1} = (G(i, j) + g_w delta_j) / D_j          (delta = 1 - ratio, subtraction-free);
+//   solve (L_i + diag G_i) w = r:  t_j = (r_j + g_w t_{j+1}) / D_j (t_N = 0),
+//                                  w_0 = t_0,  w_j = (g_w / D_j) w_{j-1} + t_j.
+//   bit line j (nodes i, top open, g_o to ground at i = M-1), eliminated from i = 0 down:
+//     E_i = G(i, j) + g_b eps_{i-1} + (i < M-1 ? g_b : g_o),  eps_{-1} = 0,
+//     eps_i = (G(i, j) + g_b eps_{i-1}) / E_i;
+//   solve (K_j + diag G_j) x = r:  s_i = (r_i + g_b s_{i-1}) / E_i (s_{-1} = 0),
+//                                  x_{M-1} = s_{M-1},  x_i = (g_b / E_i) x_{i+1} + s_i.
+// One thread per line, FP64.  Outputs in [N][M] layout (element (i, j) at j*M + i):
+//   Gt = G, St = S / (N g_scale), wl = 1/D, bl = 1/E, xg = g_o z G with z = (K_j + diag G_j)^-1 e_{M-1}.
+__global__ void prep_rows_kernel(const double* G, long sGi, long sGj, int M, int N, double gs, double gw,
+                                 double s_scale, double* Gt, float* St, double* wl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double acc = 0.0, delta = 0.0;
+  for (int j = N - 1; j >= 0; --j) {
+    const double g = G[i * sGi + j * sGj];
+    const long o = (long)j * M + i;
+    Gt[o] = g;
+    acc += g;
+    St[o] = (float)(acc * s_scale);
+    const double D = (j == 0 ? gs : gw) + g + gw * delta;
+    wl[o] = 1.0 / D;
+    delta = (g + gw * delta) / D;
+  }
+}
+
+__global__ void prep_cols_kernel(const double* Gt, int M, int N, double gb, double go, double* bl, double* xg) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double* g = Gt + (long)j * M;
+  double* e = bl + (long)j * M;
+  double* z = xg + (long)j * M;
+  double eps = 0.0;
+  for (int i = 0; i < M; ++i) {
+    const double E = g[i] + gb * eps + (i < M - 1 ? gb : go);
+    e[i] = 1.0 / E;
+    eps = (g[i] + gb * eps) / E;
+  }
+  double x = e[M - 1];  // unit current at the bottom node: s_i = 0 above it
+  for (int i = M - 1; i >= 0; --i) {
+    z[i] = go * x * g[i];
+    if (i > 0) x *= gb * e[i - 1];
+  }
+}
+
+// Field of unit-input responses for inputs k0 .. k0+K-1: F[(kk*N + j)*M + i] is node (i, j) for
+// input k = k0 + kk.  Word-line pass, one thread per (kk, i): w_i = (L_i + diag G_i)^-1
+// (G_i o u_i + g_s [i == k] e_0), u = 0 on the first pass, written over u.
+__global__ void wl_pass_kernel(const double* Gt, const double* wl, double* F, int K, int k0, int M, int N, double gs,
+                               double gw, int first) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)K * M) return;
+  const int kk = (int)(t / M), i = (int)(t - (long)kk * M);
+  double* f = F + (long)kk * N * M + i;  // node (i, j) at f[j*M]
+  double tn = 0.0;
+  for (int j = N - 1; j >= 0; --j) {
+    const long o = (long)j * M;
+    double r = first ? 0.0 : Gt[o + i] * f[o];
+    if (j == 0 && i == k0 + kk) r += gs;
+    tn = (r + gw * tn) * wl[o + i];
+    f[o] = tn;
+  }
+  double w = f[0];
+  for (int j = 1; j < N; ++j) {
+    const long o = (long)j * M;
+    w = gw * wl[o + i] * w + f[o];
+    f[o] = w;
+  }
+}
+
+// Bit-line pass, one thread per (kk, j): u_j = (K_j + diag G_j)^-1 (G_j o w_j), written over w.
+__global__ void bl_pass_kernel(const double* Gt, const double* bl, double* F, int K, int M, int N, double gb) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)K * N) return;
+  const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
+  double* f = F + ((long)kk * N + j) * M;
+  const double* g = Gt + (long)j * M;
+  const double* e = bl + (long)j * M;
+  double sp = 0.0;
+  for (int i = 0; i < M; ++i) {
+    sp = (g[i] * f[i] + gb * sp) * e[i];
+    f[i] = sp;
+  }
+  double x = f[M - 1];
+  for (int i = M - 2; i >= 0; --i) {
+    x = gb * e[i] * x + f[i];
+    f[i] = x;
+  }
+}
+
+// Sense currents of the last word-line pass: T[j*M + k] = sum_i xg(i, j) w(i, j; k).
+__global__ void line_transfer_kernel(const double* xg, const double* F, int K, int k0, int M, int N, double* T) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)K * N) return;
+  const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
+  const double* f = F + ((long)kk * N + j) * M;
+  const double* z = xg + (long)j * M;
+  double acc = 0.0;
+  for (int i = 0; i < M; ++i) acc += z[i] * f[i];
+  T[(long)j * M + k0 + kk] = acc;
+}
+
+// one block (128 threads) per row r = b*N + j: features, ideal and line-model currents, and
+// (when Iex != NULL) the target q = (Iex - I_line) / I_ideal
+__global__ void feature_kernel(const double* Gt, const float* St, const double* Tl, const double* V, const double* Iex,
+                               int M, int N, int B, int Fp, double inv_gs, double inv_vs, __nv_bfloat16* X, float* q,
+                               double* Iid, double* Iln) {
+  const long r = blockIdx.x;
+  if (r >= (long)B * N) return;
+  const int b = (int)(r / N), j = (int)(r - (long)b * N);
+  const double* gcol = Gt + (long)j * M;
+  const double* tcol = Tl + (long)j * M;
+  const float* scol = St + (long)j * M;
+  const double* v = V + (long)b * M;
+  __nv_bfloat16* xr = X + r * Fp;
+  for (int f = threadIdx.x; f < Fp; f += blockDim.x) {
+    float x = 0.0f;
+    if (f < M) {
+      x = (float)(gcol[f] * inv_gs);
+    } else if (f < 2 * M) {
+      x = (float)(v[f - M] * inv_vs);
+    } else if (f < 3 * M) {
+      x = scol[f - 2 * M];
+    }
+    xr[f] = __float2bfloat16_rn(x);
+  }
+  double pi = 0.0, pl = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    pi += v[i] * gcol[i];
+    pl += v[i] * tcol[i];
+  }
+  __shared__ double red[2][128];
+  red[0][threadIdx.x] = pi;
+  red[1][threadIdx.x] = pl;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double ideal = red[0][0], line = red[1][0];
+    if (Iid) Iid[r] = ideal;
+    if (Iln) Iln[r] = line;
+    if (q) q[r] = (Iex && ideal > 0.0) ? (float)((Iex[r] - line) / ideal) : 0.0f;
+  }
+}
+
+// Layer 3, loss and back-propagation to dZ2; one warp per row, lane l owns hidden units 8l..8l+7.
+// train: accumulates dW3, db3 and the two loss sums; predict: writes out[r] = (out0, out1).
+__global__ void head_kernel(const __nv_bfloat16* H2, const float* W3, const float* b3, const float* y, long rows,
+                            long valid, int train, float inv_rows, float* out, __nv_bfloat16* dZ2, float* dW3,
+                            float* db3, double* loss) {
+  const int lane = threadIdx.x & 31;
+  const long warp0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  float w0[8], w1[8], g0[8] = {0}, g1[8] = {0}, gb0 = 0.0f, gb1 = 0.0f;
+  double l0 = 0.0, l1 = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    w0[q] = W3[lane * 8 + q];
+    w1[q] = W3[kH + lane * 8 + q];
+  }
+  for (long r = warp0; r < rows; r += nwarps) {
+    alignas(16) __nv_bfloat16 hb[8];
+    *reinterpret_cast<uint4*>(hb) = *reinterpret_cast<const uint4*>(H2 + r * kH + lane * 8);
+    float h[8], a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      h[q] = __bfloat162float(hb[q]);
+      a0 = fmaf(w0[q], h[q], a0);
+      a1 = fmaf(w1[q], h[q], a1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    const float o0 = a0 + b3[0], o1 = a1 + b3[1];
+    if (!train) {
+      if (lane == 0 && r < valid) {
+        out[2 * r] = o0;
+        out[2 * r + 1] = o1;
+      }
+      continue;
+    }
+    float d0 = 0.0f, d1 = 0.0f;
+    if (r < valid) {
+      const float e = o0 - y[r];
+      const float t = logf(fabsf(e) + kEps);
+      d0 = 2.0f * e * inv_rows;
+      d1 = 2.0f * kLambda * (o1 - t) * inv_rows;
+      l0 += (double)e * e;
+      l1 += (double)(o1 - t) * (o1 - t);
+    }
+    alignas(16) __nv_bfloat16 db[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      db[q] = __float2bfloat16_rn(h[q] > 0.0f ? fmaf(d0, w0[q], d1 * w1[q]) : 0.0f);
+      g0[q] = fmaf(d0, h[q], g0[q]);
+      g1[q] = fmaf(d1, h[q], g1[q]);
+    }
+    *reinterpret_cast<uint4*>(dZ2 + r * kH + lane * 8) = *reinterpret_cast<const uint4*>(db);
+    gb0 += d0;
+    gb1 += d1;
+  }
+  if (!train) return;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    atomicAdd(&dW3[lane * 8 + q], g0[q]);
+    atomicAdd(&dW3[kH + lane * 8 + q], g1[q]);
+  }
+  if (lane == 0) {
+    atomicAdd(&db3[0], gb0);
+    atomicAdd(&db3[1], gb1);
+    atomicAdd(&loss[0], l0);
+    atomicAdd(&loss[1], l1);
+  }
+}
+
+// out[k] += sum over rows of D[r][k] (bias gradients); block = 256 threads = one column each
+__global__ void colsum_kernel(const __nv_bfloat16* D, long rows, long chunk, float* out) {
+  const int k = threadIdx.x;
+  const long r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  float s = 0.0f;
+  for (long r = r0; r < r1; ++r) s += __bfloat162float(D[r * kH + k]);
+  atomicAdd(&out[k], s);
+}
+
+// Adam on the flat FP32 parameters
+__global__ void adam_kernel(float* P, const float* G, float* m, float* v, int n, float lr, float b1, float b2,
+                            float c1, float c2, float eps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * g;
+  const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_bf16_kernel(const float* a, __nv_bfloat16* b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+__global__ void f32_to_bf16_rows_kernel(const float* X, long rows, int F, int Fp, __nv_bfloat16* out) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= rows * Fp) return;
+  const long r = idx / Fp;
+  const int f = (int)(idx - r * Fp);
+  out[idx] = __float2bfloat16_rn(f < F ? X[r * F + f] : 0.0f);
+}
+
+// prediction: I = I_line + I_ideal (mu + sigma n0), relative error estimate
+// c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when any entry of vector b is above the bound
+__global__ void finalize_kernel(const float* out, const double* Iid, const double* Iln, long rows, double mu,
+                                double sigma, double cal, double bound, double* I, double* est, int* flag, int N) {
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const double ii = Iid[r];
+  const double Ir = Iln[r] + ii * (mu + sigma * (double)out[2 * r]);
+  const double e = cal * sigma * exp((double)out[2 * r + 1]) * fabs(ii) / fmax(fabs(Ir), 1e-300);
+  I[r] = Ir;
+  if (est) est[r] = e;
+  if (flag && !(e <= bound)) flag[r / N] = 1;
+}
+
+// y <- (y - mu) / sigma
+__global__ void standardise_kernel(float* y, long n, float mu, float inv_sigma) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (y[i] - mu) * inv_sigma;
+}
+
+__global__ void gather_rows_kernel(const double* src, const int* idx, int n, int width, double* dst) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)n * width) return;
+  const int k = (int)(t / width), c = (int)(t - (long)k * width);
+  dst[t] = src[(long)idx[k] * width + c];
+}
+
+__global__ void scatter_rows_kernel(const double* src, const int* idx, int n, int width, double* dst) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)n * width) return;
+  const int k = (int)(t / width), c = (int)(t - (long)k * width);
+  dst[(long)idx[k] * width + c] = src[t];
+}
+
+inline long round_up_l(long a, long m) { return ((a + m - 1) / m) * m; }
+
+}  // namespace
+
+struct xbar_surrogate_s {
+  int M = 0, N = 0, F = 0, Fp = 0;
+  double R[4] = {0, 0, 0, 0};  // R_s, R_w, R_b, R_sense of the circuit the surrogate models
+  double gs = 1e-4, vs = 0.5;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  unsigned* status = nullptr;
+  DevArena A;
+  // flat FP32 parameters: W1 [kH][Fp], b1 [kH], W2 [kH][kH], b2 [kH], W3 [2][kH], b3 [2]
+  long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, np = 0;
+  float *P = nullptr, *Gr = nullptr, *Am = nullptr, *Av = nullptr;
+  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+  double* loss = nullptr;  // [2]
+  double cal = 1.0;                 // error-estimate scale (calibration)
+  double mu = 0.0, sigma = 1.0;     // target standardisation (set by the first training call)
+  int stats_set = 0;
+  int adam_t = 0;
+  // workspace (rows capacity)
+  long cap = 0;
+  Buf X, H1, H2, dZ2, dZ1, y, out, Iid, Iln, flag, idx, gV, gI;
+  // per-map line model and feature columns: [N][M]
+  int passes = 1;
+  Buf Gt, St, Tl, wl, bl, xg, field;
+  // training set
+  Buf Xall, yall;
+};
+
+static xbar_status ensure_rows(xbar_surrogate_t s, long rows) {
+  if (rows <= s->cap) return XBAR_OK;
+  const long r = round_up_l(rows, 128);
+  XB_CUDA(ensure(s->A, s->X, (size_t)r * s->Fp * 2));
+  XB_CUDA(cudaMemsetAsync(s->X.p, 0, (size_t)r * s->Fp * 2, s->st));
+  XB_CUDA(ensure(s->A, s->H1, (size_t)r * kH * 2));
+  XB_CUDA(ensure(s->A, s->H2, (size_t)r * kH * 2));
+  XB_CUDA(ensure(s->A, s->dZ2, (size_t)r * kH * 2));
+  XB_CUDA(ensure(s->A, s->dZ1, (size_t)r * kH * 2));
+  XB_CUDA(ensure(s->A, s->y, (size_t)r * 4));
+  XB_CUDA(ensure(s->A, s->out, (size_t)r * 8));
+  XB_CUDA(ensure(s->A, s->Iid, (size_t)r * 8));
+  XB_CUDA(ensure(s->A, s->Iln, (size_t)r * 8));
+  s->cap = r;
+  return XBAR_OK;
+}
+
+static xbar_status refresh_bf16(xbar_surrogate_t s) {
+  const int n1 = kH * s->Fp, n2 = kH * kH;
+  to_bf16_kernel<<<(n1 + 255) / 256, 256, 0, s->st>>>(s->P + s->oW1, s->W1b, n1);
+  to_bf16_kernel<<<(n2 + 255) / 256, 256, 0, s->st>>>(s->P + s->oW2, s->W2b, n2);
+  XB_CUDA(cudaGetLastError());
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_destroy(xbar_surrogate_t s) {
+  if (!s) return XBAR_OK;
+  cudaSetDevice(s->dev);
+  cudaStreamSynchronize(s->st);
+  s->A.free_all();
+  delete s;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_create(int M, int N, double R_s, double R_w, double R_b, double R_sense,
+                                             int line_passes, double g_scale, double v_scale, unsigned seed,
+                                             void* cuda_stream, xbar_surrogate_t* out) {
+  if (!out) return set_error(XBAR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (M < 1 || M > 1024 || N < 1) return set_error(XBAR_EINVAL, "M=%d, N=%d out of range", M, N);
+  if (line_passes < 1 || line_passes > 64) return set_error(XBAR_EINVAL, "line_passes=%d out of [1, 64]", line_passes);
+  if (!(g_scale > 0) || !(v_scale > 0) || !std::isfinite(g_scale) || !std::isfinite(v_scale))
+    return set_error(XBAR_EINVAL, "scales must be finite and > 0");
+  const double Rin[4] = {R_s, R_w, R_b, R_sense};
+  for (double r : Rin)
+    if (!(r > 0) || !std::isfinite(r)) return set_error(XBAR_EINVAL, "resistances must be finite and > 0");
+  xbar_surrogate_s* s = new xbar_surrogate_s();
+  s->M = M;
+  s->N = N;
+  s->F = 3 * M;
+  s->Fp = (int)round_up_l(s->F, 128);
+  s->gs = g_scale;
+  s->vs = v_scale;
+  for (int k = 0; k < 4; ++k) s->R[k] = Rin[k];
+  s->passes = line_passes;
+  s->st = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&s->dev);
+  s->oW1 = 0;
+  s->ob1 = s->oW1 + (long)kH * s->Fp;
+  s->oW2 = s->ob1 + kH;
+  s->ob2 = s->oW2 + (long)kH * kH;
+  s->oW3 = s->ob2 + kH;
+  s->ob3 = s->oW3 + 2 * kH;
+  s->np = s->ob3 + 2;
+  auto bail = [&](xbar_status e) {
+    xbar_surrogate_destroy(s);
+    return e;
+  };
+  if (s->A.alloc((void**)&s->P, s->np * 4) || s->A.alloc((void**)&s->Gr, s->np * 4) ||
+      s->A.alloc((void**)&s->Am, s->np * 4) || s->A.alloc((void**)&s->Av, s->np * 4) ||
+      s->A.alloc((void**)&s->W1b, (size_t)kH * s->Fp * 2) || s->A.alloc((void**)&s->W2b, (size_t)kH * kH * 2) ||
+      s->A.alloc((void**)&s->loss, 16) || s->A.alloc((void**)&s->status, 4))
+    return bail(set_error(XBAR_ENOMEM, "surrogate parameters"));
+  // He initialisation of the weights (padding columns of W1 stay zero), zero biases, small head
+  std::vector<float> h(s->np, 0.0f);
+  std::mt19937 rng(seed);
+  std::normal_distribution<float> nd(0.0f, 1.0f);
+  const float s1 = sqrtf(2.0f / s->F), s2 = sqrtf(2.0f / kH), s3 = 0.1f * sqrtf(1.0f / kH);
+  for (int o = 0; o < kH; ++o)
+    for (int f = 0; f < s->F; ++f) h[s->oW1 + (long)o * s->Fp + f] = s1 * nd(rng);
+  for (long k = 0; k < (long)kH * kH; ++k) h[s->oW2 + k] = s2 * nd(rng);
+  for (int k = 0; k < 2 * kH; ++k) h[s->oW3 + k] = s3 * nd(rng);
+  h[s->ob3 + 1] = logf(1e-3f);
+  if (cudaMemcpy(s->P, h.data(), s->np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->Am, 0, s->np * 4) != cudaSuccess || cudaMemset(s->Av, 0, s->np * 4) != cudaSuccess ||
+      cudaMemset(s->status, 0, 4) != cudaSuccess)
+    return bail(set_error(XBAR_ECUDA, "surrogate initialisation"));
+  if (refresh_bf16(s) != XBAR_OK) return bail(XBAR_ECUDA);
+  *out = s;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_params(xbar_surrogate_t s, float* get, const float* set, int* count) {
+  if (!s) return set_error(XBAR_EINVAL, "surrogate is NULL");
+  XB_CUDA(cudaSetDevice(s->dev));
+  if (count) *count = (int)s->np;
+  if (set) {
+    XB_CUDA(cudaMemcpyAsync(s->P, set, s->np * 4, cudaMemcpyDefault, s->st));
+    if (refresh_bf16(s) != XBAR_OK) return XBAR_ECUDA;
+  }
+  if (get) XB_CUDA(cudaMemcpyAsync(get, s->P, s->np * 4, cudaMemcpyDefault, s->st));
+  XB_CUDA(cudaStreamSynchronize(s->st));
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_scaling(xbar_surrogate_t s, const double* set, double* get) {
+  if (!s) return set_error(XBAR_EINVAL, "surrogate is NULL");
+  if (set) {
+    if (!(set[1] > 0) || !(set[2] > 0)) return set_error(XBAR_EINVAL, "sigma and c must be > 0");
+    s->mu = set[0];
+    s->sigma = set[1];
+    s->cal = set[2];
+    s->stats_set = 1;
+  }
+  if (get) {
+    get[0] = s->mu;
+    get[1] = s->sigma;
+    get[2] = s->cal;
+  }
+  return XBAR_OK;
+}
+
+// forward (and with train != 0 backward) on rows [0, rows) of the workspace feature matrix X;
+// `valid` rows are real (the rest are zero padding up to a multiple of 128)
+static xbar_status fwd_bwd(xbar_surrogate_t s, const __nv_bfloat16* X, long rows, long valid, const float* y,
+                           int train) {
+  const int Fp = s->Fp;
+  GemmBf16Params g;
+  memset(&g, 0, sizeof(g));
+  g.status = s->status;
+  // H1 = relu(X W1^T + b1)
+  g.M = (int)rows; g.N = kH; g.K = Fp;
+  g.A = X; g.sAm = Fp; g.sAk = 1;
+  g.B = s->W1b; g.sBn = Fp; g.sBk = 1;
+  g.mode = GEMM_EPI_BIAS_RELU; g.bias = s->P + s->ob1; g.out = (__nv_bfloat16*)s->H1.p; g.ldo = kH;
+  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
+  // H2 = relu(H1 W2^T + b2)
+  g.K = kH; g.A = (const __nv_bfloat16*)s->H1.p; g.sAm = kH;
+  g.B = s->W2b; g.sBn = kH;
+  g.bias = s->P + s->ob2; g.out = (__nv_bfloat16*)s->H2.p;
+  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
+  const int hb = (int)std::min<long>(4096, (rows + 7) / 8);
+  if (!train) {
+    head_kernel<<<hb, 256, 0, s->st>>>((const __nv_bfloat16*)s->H2.p, s->P + s->oW3, s->P + s->ob3, nullptr, rows,
+                                       valid, 0, 0.0f, (float*)s->out.p, nullptr, nullptr, nullptr, nullptr);
+    XB_CUDA(cudaGetLastError());
+    return XBAR_OK;
+  }
+  XB_CUDA(cudaMemsetAsync(s->Gr, 0, s->np * 4, s->st));
+  head_kernel<<<hb, 256, 0, s->st>>>((const __nv_bfloat16*)s->H2.p, s->P + s->oW3, s->P + s->ob3, y, rows, valid, 1,
+                                     1.0f / (float)valid, nullptr, (__nv_bfloat16*)s->dZ2.p, s->Gr + s->oW3,
+                                     s->Gr + s->ob3, s->loss);
+  XB_CUDA(cudaGetLastError());
+  const int ks = (int)std::max<long>(1, std::min<long>(64, rows / 1024));
+  // dW2 = dZ2^T H1
+  memset(&g, 0, sizeof(g));
+  g.status = s->status;
+  g.M = kH; g.N = kH; g.K = (int)rows;
+  g.A = (const __nv_bfloat16*)s->dZ2.p; g.sAm = 1; g.sAk = kH;
+  g.B = (const __nv_bfloat16*)s->H1.p; g.sBn = 1; g.sBk = kH;
+  g.mode = GEMM_EPI_STORE; g.C = s->Gr + s->oW2; g.ldc = kH; g.atomic = 1;
+  XB_CUDA(launch_gemm_bf16(g, ks, s->st));
+  // dZ1 = (dZ2 W2) o [H1 > 0]
+  memset(&g, 0, sizeof(g));
+  g.status = s->status;
+  g.M = (int)rows; g.N = kH; g.K = kH;
+  g.A = (const __nv_bfloat16*)s->dZ2.p; g.sAm = kH; g.sAk = 1;
+  g.B = s->W2b; g.sBn = 1; g.sBk = kH;
+  g.mode = GEMM_EPI_MASK; g.mask = (const __nv_bfloat16*)s->H1.p; g.ldm = kH;
+  g.out = (__nv_bfloat16*)s->dZ1.p; g.ldo = kH;
+  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
+  // dW1 = dZ1^T X
+  memset(&g, 0, sizeof(g));
+  g.status = s->status;
+  g.M = kH; g.N = Fp; g.K = (int)rows;
+  g.A = (const __nv_bfloat16*)s->dZ1.p; g.sAm = 1; g.sAk = kH;
+  g.B = X; g.sBn = 1; g.sBk = Fp;
+  g.mode = GEMM_EPI_STORE; g.C = s->Gr + s->oW1; g.ldc = Fp; g.atomic = 1;
+  XB_CUDA(launch_gemm_bf16(g, ks, s->st));
+  // bias gradients
+  const long chunk = 512;
+  const int nb = (int)((rows + chunk - 1) / chunk);
+  colsum_kernel<<<nb, kH, 0, s->st>>>((const __nv_bfloat16*)s->dZ2.p, rows, chunk, s->Gr + s->ob2);
+  colsum_kernel<<<nb, kH, 0, s->st>>>((const __nv_bfloat16*)s->dZ1.p, rows, chunk, s->Gr + s->ob1);
+  XB_CUDA(cudaGetLastError());
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_grad(xbar_surrogate_t s, int R, const float* X, const float* y, double* loss,
+                                           float* grad) {
+  if (!s || !X || !y || R < 1) return set_error(XBAR_EINVAL, "bad arguments");
+  XB_CUDA(cudaSetDevice(s->dev));
+  const long rows = round_up_l(R, 128);
+  if (ensure_rows(s, rows) != XBAR_OK) return XBAR_ENOMEM;
+  float *dXf = nullptr, *dy = nullptr;
+  XB_CUDA(cudaMalloc(&dXf, (size_t)R * s->F * 4));
+  XB_CUDA(cudaMalloc(&dy, (size_t)rows * 4));
+  XB_CUDA(cudaMemcpyAsync(dXf, X, (size_t)R * s->F * 4, cudaMemcpyDefault, s->st));
+  XB_CUDA(cudaMemsetAsync(dy, 0, (size_t)rows * 4, s->st));
+  XB_CUDA(cudaMemcpyAsync(dy, y, (size_t)R * 4, cudaMemcpyDefault, s->st));
+  standardise_kernel<<<(R + 255) / 256, 256, 0, s->st>>>(dy, R, (float)s->mu, (float)(1.0 / s->sigma));
+  XB_CUDA(cudaMemsetAsync(s->X.p, 0, (size_t)rows * s->Fp * 2, s->st));
+  const long n = (long)R * s->Fp;
+  f32_to_bf16_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s->st>>>(dXf, R, s->F, s->Fp,
+                                                                           (__nv_bfloat16*)s->X.p);
+  XB_CUDA(cudaMemsetAsync(s->loss, 0, 16, s->st));
+  xbar_status st = fwd_bwd(s, (const __nv_bfloat16*)s->X.p, rows, R, dy, 1);
+  double l[2] = {0, 0};
+  unsigned dst = 0;
+  if (st == XBAR_OK) {
+    XB_CUDA(cudaMemcpyAsync(l, s->loss, 16, cudaMemcpyDeviceToHost, s->st));
+    if (grad) XB_CUDA(cudaMemcpyAsync(grad, s->Gr, s->np * 4, cudaMemcpyDefault, s->st));
+    XB_CUDA(cudaMemcpyAsync(&dst, s->status, 4, cudaMemcpyDeviceToHost, s->st));
+    XB_CUDA(cudaStreamSynchronize(s->st));
+    if (loss) {
+      loss[0] = l[0] / R;
+      loss[1] = l[1] / R;
+    }
+  }
+  cudaFree(dXf);
+  cudaFree(dy);
+  if (st == XBAR_OK && dst)
+    return set_error(dst & XBAR_DEV_TIMEOUT ? XBAR_ETIMEOUT : XBAR_ECUDA, "device status 0x%x", dst);
+  return st;
+}
+
+// line model and feature columns of one map (G(i, j) = G[i*sGi + j*sGj], device), then features,
+// ideal and line-model currents (and targets when Iex != NULL) of its B vectors into X, q, Iid, Iln
+static xbar_status build_features(xbar_surrogate_t s, const double* G, long sGi, long sGj, int B, const double* V,
+                                  const double* Iex, __nv_bfloat16* X, float* q, double* Iid, double* Iln) {
+  const int M = s->M, N = s->N;
+  const size_t mn = (size_t)M * N;
+  // inputs per chunk of the response field: at most 256 MiB of it
+  const int K = (int)std::max<size_t>(1, std::min<size_t>((size_t)M, ((size_t)256 << 20) / (mn * 8)));
+  XB_CUDA(ensure(s->A, s->Gt, mn * 8));
+  XB_CUDA(ensure(s->A, s->St, mn * 4));
+  XB_CUDA(ensure(s->A, s->Tl, mn * 8));
+  XB_CUDA(ensure(s->A, s->wl, mn * 8));
+  XB_CUDA(ensure(s->A, s->bl, mn * 8));
+  XB_CUDA(ensure(s->A, s->xg, mn * 8));
+  XB_CUDA(ensure(s->A, s->field, (size_t)K * mn * 8));
+  const double gs = 1.0 / s->R[0], gw = 1.0 / s->R[1], gb = 1.0 / s->R[2], go = 1.0 / s->R[3];
+  double* Gt = (double*)s->Gt.p;
+  double* F = (double*)s->field.p;
+  prep_rows_kernel<<<(M + 127) / 128, 128, 0, s->st>>>(G, sGi, sGj, M, N, gs, gw, 1.0 / (N * s->gs), Gt,
+                                                       (float*)s->St.p, (double*)s->wl.p);
+  prep_cols_kernel<<<(N + 127) / 128, 128, 0, s->st>>>(Gt, M, N, gb, go, (double*)s->bl.p, (double*)s->xg.p);
+  for (int k0 = 0; k0 < M; k0 += K) {
+    const int Kc = std::min(K, M - k0);
+    const unsigned gm = (unsigned)(((long)Kc * M + 127) / 128), gn = (unsigned)(((long)Kc * N + 127) / 128);
+    for (int p = 0; p < s->passes; ++p) {
+      wl_pass_kernel<<<gm, 128, 0, s->st>>>(Gt, (const double*)s->wl.p, F, Kc, k0, M, N, gs, gw, p == 0);
+      if (p + 1 < s->passes) bl_pass_kernel<<<gn, 128, 0, s->st>>>(Gt, (const double*)s->bl.p, F, Kc, M, N, gb);
+    }
+    line_transfer_kernel<<<gn, 128, 0, s->st>>>((const double*)s->xg.p, F, Kc, k0, M, N, (double*)s->Tl.p);
+  }
+  feature_kernel<<<(unsigned)((long)B * N), 128, 0, s->st>>>(Gt, (const float*)s->St.p, (const double*)s->Tl.p, V,
+                                                             Iex, M, N, B, s->Fp, 1.0 / s->gs, 1.0 / s->vs, X, q, Iid,
+                                                             Iln);
+  XB_CUDA(cudaGetLastError());
+  return XBAR_OK;
+}
+
+// device copies of one map's (G, V, I) when they are host pointers
+struct MapData {
+  const double *G = nullptr, *V = nullptr, *I = nullptr;
+  std::vector<void*> owned;
+  ~MapData() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+static xbar_status map_to_device(xbar_surrogate_t s, const double* G, int B, const double* V, const double* I,
+                                 MapData& d) {
+  auto put = [&](const double* src, size_t n, const double** dst) -> xbar_status {
+    if (!src) {
+      *dst = nullptr;
+      return XBAR_OK;
+    }
+    if (is_device_ptr(src)) {
+      *dst = src;
+      return XBAR_OK;
+    }
+    void* p = nullptr;
+    XB_CUDA(cudaMalloc(&p, n * 8));
+    d.owned.push_back(p);
+    XB_CUDA(cudaMemcpyAsync(p, src, n * 8, cudaMemcpyHostToDevice, s->st));
+    *dst = (const double*)p;
+    return XBAR_OK;
+  };
+  xbar_status st = put(G, (size_t)s->M * s->N, &d.G);
+  if (st == XBAR_OK) st = put(V, (size_t)B * s->M, &d.V);
+  if (st == XBAR_OK) st = put(I, (size_t)B * s->N, &d.I);
+  return st;
+}
+
+extern "C" xbar_status xbar_surrogate_train(xbar_surrogate_t s, int n_maps, const double* const* G, const int* B,
+                                            const double* const* V, const double* const* I, int epochs,
+                                            int batch_rows, double lr, unsigned seed, double* loss_per_epoch) {
+  if (!s || n_maps < 1 || !G || !B || !V || !I || epochs < 0) return set_error(XBAR_EINVAL, "bad arguments");
+  if (batch_rows < 128 || batch_rows % 128) return set_error(XBAR_EINVAL, "batch_rows must be a multiple of 128");
+  XB_CUDA(cudaSetDevice(s->dev));
+  long total = 0;
+  for (int m = 0; m < n_maps; ++m) {
+    if (B[m] < 1) return set_error(XBAR_EINVAL, "B[%d] < 1", m);
+    total += (long)B[m] * s->N;
+  }
+  const long padded = round_up_l(total, batch_rows);
+  XB_CUDA(ensure(s->A, s->Xall, (size_t)padded * s->Fp * 2));
+  XB_CUDA(ensure(s->A, s->yall, (size_t)padded * 4));
+  XB_CUDA(cudaMemsetAsync(s->Xall.p, 0, (size_t)padded * s->Fp * 2, s->st));
+  XB_CUDA(cudaMemsetAsync(s->yall.p, 0, (size_t)padded * 4, s->st));
+  long r0 = 0;
+  for (int m = 0; m < n_maps; ++m) {
+    MapData d;
+    xbar_status st = map_to_device(s, G[m], B[m], V[m], I[m], d);
+    if (st != XBAR_OK) return st;
+    st = build_features(s, d.G, s->N, 1, B[m], d.V, d.I, (__nv_bfloat16*)s->Xall.p + r0 * s->Fp,
+                        (float*)s->yall.p + r0, nullptr, nullptr);
+    if (st != XBAR_OK) return st;
+    XB_CUDA(cudaStreamSynchronize(s->st));  // host copies of this map may be released
+    r0 += (long)B[m] * s->N;
+  }
+  if (!s->stats_set) {  // standardisation of the target from this first training set
+    std::vector<float> hy(total);
+    XB_CUDA(cudaMemcpy(hy.data(), s->yall.p, (size_t)total * 4, cudaMemcpyDeviceToHost));
+    double m1 = 0.0, m2 = 0.0;
+    for (long k = 0; k < total; ++k) m1 += hy[k];
+    m1 /= total;
+    for (long k = 0; k < total; ++k) m2 += (hy[k] - m1) * (hy[k] - m1);
+    s->mu = m1;
+    s->sigma = std::max(sqrt(m2 / total), 1e-6);
+    s->stats_set = 1;
+  }
+  standardise_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s->st>>>((float*)s->yall.p, total, (float)s->mu,
+                                                                        (float)(1.0 / s->sigma));
+  XB_CUDA(cudaGetLastError());
+  if (ensure_rows(s, batch_rows) != XBAR_OK) return XBAR_ENOMEM;
+  const long nb = padded / batch_rows;
+  std::vector<long> order(nb);
+  for (long k = 0; k < nb; ++k) order[k] = k;
+  std::mt19937 rng(seed);
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::shuffle(order.begin(), order.end(), rng);
+    XB_CUDA(cudaMemsetAsync(s->loss, 0, 16, s->st));
+    for (long k = 0; k < nb; ++k) {
+      const long start = order[k] * batch_rows;
+      const long valid = std::min<long>(batch_rows, total - start);
+      if (valid <= 0) continue;
+      xbar_status st = fwd_bwd(s, (const __nv_bfloat16*)s->Xall.p + start * s->Fp, batch_rows, valid,
+                               (const float*)s->yall.p + start, 1);
+      if (st != XBAR_OK) return st;
+      ++s->adam_t;
+      const float c1 = 1.0f - powf(b1, (float)s->adam_t), c2 = 1.0f - powf(b2, (float)s->adam_t);
+      adam_kernel<<<(unsigned)((s->np + 255) / 256), 256, 0, s->st>>>(s->P, s->Gr, s->Am, s->Av, (int)s->np, (float)lr,
+                                                                       b1, b2, c1, c2, 1e-8f);
+      if (refresh_bf16(s) != XBAR_OK) return XBAR_ECUDA;
+    }
+    double l[2];
+    XB_CUDA(cudaMemcpyAsync(l, s->loss, 16, cudaMemcpyDeviceToHost, s->st));
+    XB_CUDA(cudaStreamSynchronize(s->st));
+    if (loss_per_epoch) {
+      loss_per_epoch[2 * ep] = l[0] / total;
+      loss_per_epoch[2 * ep + 1] = l[1] / total;
+    }
+  }
+  unsigned dst = 0;
+  XB_CUDA(cudaMemcpy(&dst, s->status, 4, cudaMemcpyDeviceToHost));
+  if (dst) return set_error(dst & XBAR_DEV_TIMEOUT ? XBAR_ETIMEOUT : XBAR_ECUDA, "device status 0x%x", dst);
+  return XBAR_OK;
+}
+
+// predict one map held in device memory (G(i,j) = G[i*sGi + j*sGj]); I, est, flag on the device
+static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, long sGj, int B, const double* V,
+                               double* I, double* est, int* flag, double bound) {
+  const long rows = (long)B * s->N, padded = round_up_l(rows, 128);
+  if (ensure_rows(s, padded) != XBAR_OK) return XBAR_ENOMEM;
+  xbar_status st = build_features(s, G, sGi, sGj, B, V, nullptr, (__nv_bfloat16*)s->X.p, nullptr,
+                                  (double*)s->Iid.p, (double*)s->Iln.p);
+  if (st != XBAR_OK) return st;
+  st = fwd_bwd(s, (const __nv_bfloat16*)s->X.p, padded, rows, nullptr, 0);
+  if (st != XBAR_OK) return st;
+  finalize_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s->st>>>((const float*)s->out.p, (const double*)s->Iid.p,
+                                                                      (const double*)s->Iln.p, rows, s->mu, s->sigma,
+                                                                      s->cal, bound, I, est, flag, s->N);
+  XB_CUDA(cudaGetLastError());
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_predict(xbar_surrogate_t s, const double* G, int B, const double* V, double* I,
+                                              double* err_est) {
+  if (!s || !G || !V || !I || B < 0) return set_error(XBAR_EINVAL, "bad arguments");
+  if (B == 0) return XBAR_OK;
+  XB_CUDA(cudaSetDevice(s->dev));
+  MapData d;
+  xbar_status st = map_to_device(s, G, B, V, nullptr, d);
+  if (st != XBAR_OK) return st;
+  const size_t n = (size_t)B * s->N;
+  const bool idev = is_device_ptr(I), edev = !err_est || is_device_ptr(err_est);
+  double *dI = I, *dE = err_est;
+  if (!idev) {
+    XB_CUDA(ensure(s->A, s->gI, n * 8));
+    dI = (double*)s->gI.p;
+  }
+  if (err_est && !edev) {
+    XB_CUDA(ensure(s->A, s->gV, n * 8));
+    dE = (double*)s->gV.p;
+  }
+  st = predict_map(s, d.G, s->N, 1, B, d.V, dI, dE, nullptr, 0.0);
+  if (st != XBAR_OK) return st;
+  if (!idev) XB_CUDA(cudaMemcpyAsync(I, dI, n * 8, cudaMemcpyDeviceToHost, s->st));
+  if (err_est && !edev) XB_CUDA(cudaMemcpyAsync(err_est, dE, n * 8, cudaMemcpyDeviceToHost, s->st));
+  XB_CUDA(cudaStreamSynchronize(s->st));
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_calibrate(xbar_surrogate_t s, int n_maps, const double* const* G, const int* B,
+                                                const double* const* V, const double* const* I, double quantile,
+                                                double* scale_out) {
+  if (!s || n_maps < 1 || !G || !B || !V || !I || !(quantile > 0.0 && quantile <= 1.0))
+    return set_error(XBAR_EINVAL, "bad arguments");
+  XB_CUDA(cudaSetDevice(s->dev));
+  const double save = s->cal;
+  s->cal = 1.0;
+  std::vector<double> ratios;
+  for (int m = 0; m < n_maps; ++m) {
+    MapData d;
+    xbar_status st = map_to_device(s, G[m], B[m], V[m], I[m], d);
+    if (st != XBAR_OK) return st;
+    const size_t n = (size_t)B[m] * s->N;
+    std::vector<double> hp(n), he(n), hx(n);
+    double *dP = nullptr, *dE = nullptr;
+    XB_CUDA(cudaMalloc(&dP, n * 8));
+    XB_CUDA(cudaMalloc(&dE, n * 8));
+    st = predict_map(s, d.G, s->N, 1, B[m], d.V, dP, dE, nullptr, 0.0);
+    if (st == XBAR_OK) {
+      cudaMemcpyAsync(hp.data(), dP, n * 8, cudaMemcpyDeviceToHost, s->st);
+      cudaMemcpyAsync(he.data(), dE, n * 8, cudaMemcpyDeviceToHost, s->st);
+      cudaMemcpyAsync(hx.data(), d.I, n * 8, cudaMemcpyDeviceToHost, s->st);
+      cudaStreamSynchronize(s->st);
+    }
+    cudaFree(dP);
+    cudaFree(dE);
+    if (st != XBAR_OK) {
+      s->cal = save;
+      return st;
+    }
+    for (size_t k = 0; k < n; ++k)
+      if (hx[k] != 0.0 && he[k] > 0.0) ratios.push_back(fabs(hp[k] - hx[k]) / fabs(hx[k]) / he[k]);
+  }
+  if (ratios.empty()) {
+    s->cal = save;
+    return set_error(XBAR_EINVAL, "no calibration samples");
+  }
+  const size_t q = std::min(ratios.size() - 1, (size_t)ceil(quantile * ratios.size()) - 1);
+  std::nth_element(ratios.begin(), ratios.begin() + q, ratios.end());
+  s->cal = std::max(ratios[q], 1e-30);
+  if (scale_out) *scale_out = s->cal;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_surrogate_solve(xbar_surrogate_t s, xbar_t exact, int B, const double* V, double* I,
+                                            double bound, double* err_est, xbar_solve_info* info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!s || !exact || !V || !I || B < 0 || !(bound > 0)) return set_error(XBAR_EINVAL, "bad arguments");
+  if (exact->m.M != s->M || exact->m.N != s->N) return set_error(XBAR_EINVAL, "handle size differs from the surrogate");
+  for (int k = 0; k < 4; ++k)
+    if (exact->R[k] != s->R[k]) return set_error(XBAR_EINVAL, "handle circuit differs from the surrogate's");
+  if (!is_device_ptr(V) || !is_device_ptr(I) || (err_est && !is_device_ptr(err_est)))
+    return set_error(XBAR_EINVAL, "xbar_surrogate_solve takes device pointers");
+  if (B == 0) return XBAR_OK;
+  XB_CUDA(cudaSetDevice(s->dev));
+  XB_CUDA(cudaStreamSynchronize(exact->st));  // the handle's conductances are written on its stream
+  XB_CUDA(ensure(s->A, s->flag, (size_t)B * 4));
+  XB_CUDA(cudaMemsetAsync(s->flag.p, 0, (size_t)B * 4, s->st));
+  // the handle holds G transposed: G(i, j) = Gc[j*Mp + i]
+  xbar_status st = predict_map(s, exact->m.Gc, 1, exact->m.Mp, B, V, I, err_est, (int*)s->flag.p, bound);
+  if (st != XBAR_OK) return st;
+  std::vector<int> flag(B);
+  XB_CUDA(cudaMemcpyAsync(flag.data(), s->flag.p, (size_t)B * 4, cudaMemcpyDeviceToHost, s->st));
+  XB_CUDA(cudaStreamSynchronize(s->st));
+  std::vector<int> idx;
+  for (int b = 0; b < B; ++b)
+    if (flag[b]) idx.push_back(b);
+  if (info) info->n_fallback = (int)idx.size();
+  if (idx.empty()) return XBAR_OK;
+  // fall back to the exact method for the flagged vectors (factoring the map if it is not yet)
+  if (!exact->factored) {
+    st = xbar_factor(exact, XBAR_FP32_IR);
+    if (st != XBAR_OK) return st;
+  }
+  const int nf = (int)idx.size(), M = s->M, N = s->N;
+  XB_CUDA(ensure(s->A, s->idx, (size_t)nf * 4));
+  XB_CUDA(ensure(s->A, s->gV, (size_t)nf * M * 8));
+  XB_CUDA(ensure(s->A, s->gI, (size_t)nf * N * 8));
+  XB_CUDA(cudaMemcpyAsync(s->idx.p, idx.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, s->st));
+  gather_rows_kernel<<<(unsigned)(((long)nf * M + 255) / 256), 256, 0, s->st>>>(V, (const int*)s->idx.p, nf, M,
+                                                                               (double*)s->gV.p);
+  XB_CUDA(cudaGetLastError());
+  XB_CUDA(cudaStreamSynchronize(s->st));  // the exact handle runs on its own stream
+  xbar_solve_info ein;
+  st = xbar_solve(exact, nf, (const double*)s->gV.p, (double*)s->gI.p, nullptr, nullptr, 1e-8, 10, &ein);
+  if (st != XBAR_OK) return st;
+  XB_CUDA(cudaStreamSynchronize(exact->st));
+  scatter_rows_kernel<<<(unsigned)(((long)nf * N + 255) / 256), 256, 0, s->st>>>((const double*)s->gI.p,
+                                                                                (const int*)s->idx.p, nf, N, I);
+  XB_CUDA(cudaGetLastError());
+  XB_CUDA(cudaStreamSynchronize(s->st));
+  if (info) {
+    info->iters = ein.iters;
+    info->max_rel_dI = ein.max_rel_dI;
+    info->resid_inf = ein.resid_inf;
+    info->err_est = ein.err_est;
+  }
+  return XBAR_OK;
+}

@@ -90,12 +90,28 @@ def load(build_if_missing: bool = True):
     lib.xbar_profile_enable.argtypes = [_vp, ctypes.c_int]
     lib.xbar_profile_read.argtypes = [_vp, ctypes.POINTER(Profile), ctypes.c_int]
     lib.xbar_destroy.argtypes = [_vp]
+    _pp, _ip = ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)
+    lib.xbar_surrogate_create.argtypes = ([ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [ctypes.c_int]
+                                          + [ctypes.c_double] * 2 + [ctypes.c_uint, _vp, _pp])
+    lib.xbar_surrogate_params.argtypes = [_vp, _vp, _vp, _ip]
+    lib.xbar_surrogate_scaling.argtypes = [_vp, _vp, _vp]
+    lib.xbar_surrogate_grad.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    lib.xbar_surrogate_train.argtypes = [_vp, ctypes.c_int, _pp, _ip, _pp, _pp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_uint, _vp]
+    lib.xbar_surrogate_calibrate.argtypes = [_vp, ctypes.c_int, _pp, _ip, _pp, _pp, ctypes.c_double, _vp]
+    lib.xbar_surrogate_predict.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp]
+    lib.xbar_surrogate_solve.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_double, _vp,
+                                         ctypes.POINTER(SolveInfo)]
+    lib.xbar_surrogate_destroy.argtypes = [_vp]
     lib.xbar_last_error.restype = ctypes.c_char_p
     lib.xbar_version.restype = ctypes.c_char_p
     for f in ("xbar_assemble", "xbar_factor", "xbar_solve", "xbar_sync", "xbar_destroy", "xbar_set_conductances",
               "xbar_profile_enable", "xbar_profile_read", "xbar_solve_noalloc", "xbar_set_option",
               "xbar_batch_create", "xbar_batch_run", "xbar_batch_autotune", "xbar_batch_tile",
-              "xbar_batch_destroy"):
+              "xbar_batch_destroy", "xbar_surrogate_create", "xbar_surrogate_params", "xbar_surrogate_grad",
+              "xbar_surrogate_scaling",
+              "xbar_surrogate_train", "xbar_surrogate_calibrate", "xbar_surrogate_predict",
+              "xbar_surrogate_solve", "xbar_surrogate_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -111,16 +127,17 @@ def _check(status):
 
 
 def _ptr(a, dtype=np.float64):
-    """Data pointer of a contiguous float64 torch tensor or numpy array (None -> NULL)."""
+    """Data pointer of a contiguous torch tensor or numpy array of `dtype` (None -> NULL)."""
     if a is None:
         return None
+    name = np.dtype(dtype).name
     if hasattr(a, "data_ptr"):
         import torch
-        if a.dtype != torch.float64 or not a.is_contiguous():
-            raise TypeError("expected a contiguous float64 tensor")
+        if a.dtype != getattr(torch, name) or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {name} tensor")
         return a.data_ptr()
     if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
-        raise TypeError("expected a contiguous float64 numpy array")
+        raise TypeError(f"expected a contiguous {name} numpy array")
     return a.ctypes.data
 
 
@@ -239,6 +256,100 @@ class Batch:
     def destroy(self):
         if self.handle:
             load().xbar_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """xbar_surrogate_*: the learned per-column estimate of the currents, with exact fallback."""
+
+    def __init__(self, M, N, circuit, passes=2, g_scale=1e-4, v_scale=0.5, seed=0, stream=None):
+        """circuit: (R_s, R_w, R_b, R_sense) of the crossbars modelled; passes: line-model passes."""
+        h = _vp()
+        _check(load().xbar_surrogate_create(int(M), int(N), *[float(r) for r in circuit], int(passes), g_scale,
+                                            v_scale, seed, _stream_ptr(stream), ctypes.byref(h)))
+        self.passes = int(passes)
+        self.handle = h.value
+        self.M, self.N = int(M), int(N)
+
+    def n_params(self):
+        n = ctypes.c_int()
+        _check(load().xbar_surrogate_params(self.handle, None, None, ctypes.byref(n)))
+        return n.value
+
+    def get_params(self):
+        out = np.empty(self.n_params(), dtype=np.float32)
+        _check(load().xbar_surrogate_params(self.handle, _ptr(out, np.float32), None, None))
+        return out
+
+    def set_params(self, P):
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        _check(load().xbar_surrogate_params(self.handle, None, _ptr(P, np.float32), None))
+
+    def scaling(self, mu=None, sigma=None, c=None):
+        """Get (and, given values, first set) the scalars (mu, sigma, c) around the network."""
+        cur = np.zeros(3)
+        _check(load().xbar_surrogate_scaling(self.handle, None, _ptr(cur)))
+        if mu is not None or sigma is not None or c is not None:
+            new = np.array([cur[0] if mu is None else mu, cur[1] if sigma is None else sigma,
+                            cur[2] if c is None else c], dtype=np.float64)
+            _check(load().xbar_surrogate_scaling(self.handle, _ptr(new), _ptr(cur)))
+        return tuple(float(v) for v in cur)
+
+    def grad(self, X, y):
+        """X: R x 3M float32 features, y: R targets q -> (loss[2], flat gradient float32)."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = np.zeros(2)
+        g = np.empty(self.n_params(), dtype=np.float32)
+        _check(load().xbar_surrogate_grad(self.handle, int(X.shape[0]), _ptr(X, np.float32), _ptr(y, np.float32),
+                                          _ptr(loss), _ptr(g, np.float32)))
+        return loss, g
+
+    @staticmethod
+    def _maps(Gs, Vs, Is):
+        n = len(Gs)
+        Garr = (_vp * n)(*[_ptr(G) for G in Gs])
+        Varr = (_vp * n)(*[_ptr(V) for V in Vs])
+        Iarr = (_vp * n)(*[_ptr(I) for I in Is])
+        Barr = (ctypes.c_int * n)(*[int(V.shape[0]) for V in Vs])
+        return n, Garr, Barr, Varr, Iarr
+
+    def train(self, Gs, Vs, Is, epochs=10, batch_rows=4096, lr=1e-3, seed=0):
+        """Gs[m]: M x N, Vs[m]: B_m x M, Is[m]: B_m x N exact currents -> losses [epochs x 2]."""
+        n, Garr, Barr, Varr, Iarr = self._maps(Gs, Vs, Is)
+        losses = np.zeros((max(epochs, 1), 2))
+        _check(load().xbar_surrogate_train(self.handle, n, Garr, Barr, Varr, Iarr, int(epochs), int(batch_rows), lr,
+                                           seed, _ptr(losses)))
+        return losses[:epochs]
+
+    def calibrate(self, Gs, Vs, Is, quantile=0.99):
+        n, Garr, Barr, Varr, Iarr = self._maps(Gs, Vs, Is)
+        c = ctypes.c_double()
+        _check(load().xbar_surrogate_calibrate(self.handle, n, Garr, Barr, Varr, Iarr, quantile, ctypes.byref(c)))
+        return c.value
+
+    def predict(self, G, V, I, err_est=None):
+        _check(load().xbar_surrogate_predict(self.handle, _ptr(G), int(V.shape[0]), _ptr(V), _ptr(I),
+                                             _ptr(err_est)))
+
+    def solve(self, exact, V, I, bound=0.01, err_est=None, raise_on_error=True):
+        """Predict for the map of Crossbar `exact`, solving vectors above `bound` exactly (device tensors)."""
+        info = SolveInfo()
+        st = load().xbar_surrogate_solve(self.handle, exact.handle, int(V.shape[0]), _ptr(V), _ptr(I), bound,
+                                         _ptr(err_est), ctypes.byref(info))
+        if raise_on_error:
+            _check(st)
+        return st, info.as_dict()
+
+    def destroy(self):
+        if self.handle:
+            load().xbar_surrogate_destroy(self.handle)
             self.handle = 0
 
     def __del__(self):
