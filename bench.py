@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch size (profiling runs)")
+    ap.add_argument("--epochs", type=int, default=24, help="surrogate workload: training epochs")
+    ap.add_argument("--line-passes", type=int, default=2, help="surrogate workload: line-model passes")
     return ap.parse_args()
 
 
@@ -449,12 +451,158 @@ def run_tiles(args):
     d.close()
 
 
+def run_surrogate(args):
+    """Learned surrogate on 128 x 128 maps: exact solves make the data, the GPU trains, calibrates,
+    then predicts 50 held-out maps x 1000 vectors with exact fallback above 1% estimated error."""
+    import torch
+
+    from paper_2410_19993_gb300 import inputs, xbar
+
+    d = Dist()
+    torch.cuda.set_device(d.local)
+    w = inputs.WORKLOADS["surrogate128"]
+    x = w.extra
+    M, N = w.M, w.N
+    R = w.circuits[0].as_tuple()
+    bound = 0.01
+    stream = torch.cuda.current_stream()
+    xb = xbar.Crossbar.assemble(torch.zeros((M, N), dtype=torch.float64, device="cuda") + 1e-5, *R, stream=stream)
+
+    def exact(G, V, I):
+        xb.set_conductances(G)
+        xb.factor("fp32_ir")
+        xb.solve(V, I, tol=TOL, max_iter=10)
+
+    def maps(n, B, seed):
+        out = []
+        for G, V in inputs.maps(n, M, N, B, seed=seed + 1000 * d.rank, g_lo=w.g_lo, g_hi=w.g_hi, v_max=w.v_max):
+            out.append((torch.from_numpy(G).cuda(), torch.from_numpy(V).cuda(),
+                        torch.zeros((B, N), dtype=torch.float64, device="cuda")))
+        return out
+
+    train = maps(x["train_maps"], x["train_B"], x["train_seed"])
+    calib = maps(x["calib_maps"], x["calib_B"], x["calib_seed"])
+    test = maps(x["test_maps"], x["test_B"], x["test_seed"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for G, V, I in train + calib:
+        exact(G, V, I)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+
+    s = xbar.Surrogate(M, N, R, passes=args.line_passes, g_scale=w.g_hi, v_scale=w.v_max, seed=5)
+    t0 = time.perf_counter()
+    e1 = max(1, int(round(0.75 * args.epochs)))
+    l1 = s.train([G for G, _, _ in train], [V for _, V, _ in train], [I for _, _, I in train],
+                 epochs=e1, batch_rows=4096, lr=1e-3, seed=9)
+    l2 = s.train([G for G, _, _ in train], [V for _, V, _ in train], [I for _, _, I in train],
+                 epochs=args.epochs - e1, batch_rows=4096, lr=3e-4, seed=10)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    c = s.calibrate([G for G, _, _ in calib], [V for _, V, _ in calib], [I for _, _, I in calib], quantile=0.99)
+    losses = np.concatenate([l1, l2]) if len(l2) else l1
+
+    Iex = [torch.zeros_like(I) for _, _, I in test]
+    Isur = [torch.zeros_like(I) for _, _, I in test]
+    est = [torch.zeros_like(I) for _, _, I in test]
+    nfb = [0]
+
+    def step_exact():
+        for (G, V, _), I in zip(test, Iex):
+            exact(G, V, I)
+
+    def step_sur():
+        nfb[0] = 0
+        for (G, V, _), I, e in zip(test, Isur, est):
+            xb.set_conductances(G)
+            _, info = s.solve(xb, V, I, bound=bound, err_est=e)
+            nfb[0] += info["n_fallback"]
+
+    def timed(fn, K):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        d.barrier()
+        t1 = time.perf_counter()
+        for _ in range(K):
+            fn()
+        torch.cuda.synchronize()
+        return d.max(time.perf_counter() - t1)
+
+    clocks = Clocks(d.local)
+    clocks.start()
+    t_sur = timed(step_sur, args.steps)
+    clk = clocks.stop()
+    t_ex = timed(step_exact, max(1, args.steps // 2))
+    n_vec = sum(V.shape[0] for _, V, _ in test)
+    value = d.sum(float(n_vec * args.steps)) / t_sur
+    exact_value = d.sum(float(n_vec * max(1, args.steps // 2))) / t_ex
+
+    # accuracy against the exact solves, and of the estimates the network corrects
+    zero = xbar.Surrogate(M, N, R, passes=args.line_passes, g_scale=w.g_hi, v_scale=w.v_max)
+    zero.set_params(np.zeros(zero.n_params(), dtype=np.float32))
+    e_sur, e_net, e_line, e_ideal, acc_bad = [], [], [], [], 0
+    for (G, V, _), Ie, Is_, ee in zip(test, Iex, Isur, est):
+        Ie_h = Ie.cpu().numpy()
+        Ip = torch.zeros_like(Ie)
+        s.predict(G, V, Ip)
+        Il = torch.zeros_like(Ie)
+        zero.predict(G, V, Il)
+        Iid = (V @ G).cpu().numpy()
+        rel = lambda a: np.abs(a - Ie_h) / np.abs(Ie_h)
+        e_sur.append(rel(Is_.cpu().numpy()))
+        e_net.append(rel(Ip.cpu().numpy()))
+        e_line.append(rel(Il.cpu().numpy()))
+        e_ideal.append(rel(Iid))
+        accepted = np.all(ee.cpu().numpy() <= bound, axis=1)
+        acc_bad += int((e_sur[-1][accepted] > bound).sum())
+    zero.destroy()
+    q = lambda a: {"median": float(np.median(a)), "p99": float(np.quantile(a, 0.99)), "max": float(np.max(a))}
+    cat = lambda a: np.concatenate(a).ravel()
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        G0, V0 = inputs.maps(1, M, N, x["test_B"], seed=x["test_seed"])[0]
+        cpu, _ = cpu_baseline(M, N, G0, R, V0, args.cpu_sample)
+    out = {
+        "metric": "surrogate solves/s (per-column MLP + exact fallback above 1% estimated error)",
+        "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_sur / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 network, fp64 line model", "data": "synthetic",
+        "config": {"workload": "surrogate128", "M": M, "N": N, "R_s": R[0], "R_w": R[1], "R_b": R[2],
+                   "R_sense": R[3], "train": f"{x['train_maps']} maps x {x['train_B']} vectors",
+                   "calib": f"{x['calib_maps']} maps x {x['calib_B']} vectors",
+                   "test": f"{x['test_maps']} held-out maps x {x['test_B']} vectors", "bound": bound,
+                   "line_passes": args.line_passes, "epochs": args.epochs, "batch_rows": 4096,
+                   "step": "per test map: set_conductances + surrogate solve (line model, features, network, "
+                           "fallback solves)", "parallelism": f"replicas{d.world}"},
+        "exact_baseline": {"value": exact_value, "unit": UNIT,
+                           "step": "per test map: set_conductances + factor(fp32_ir) + solve(tol 1e-8)"},
+        "speedup_vs_exact": value / exact_value,
+        "fallback_vectors_per_step": nfb[0], "vectors_per_step": n_vec,
+        "accepted_columns_above_bound": acc_bad,
+        "rel_err": {"surrogate_with_fallback": q(cat(e_sur)), "network": q(cat(e_net)),
+                    "line_model_alone": q(cat(e_line)), "ideal_mvm": q(cat(e_ideal))},
+        "training": {"datagen_s": t_data, "train_s": t_train, "rows": x["train_maps"] * x["train_B"] * N,
+                     "loss_first": losses[0].tolist(), "loss_last": losses[-1].tolist(), "calibration_c": c,
+                     "scaling": s.scaling()},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    if d.rank == 0:
+        print(json.dumps(out), flush=True)
+    s.destroy()
+    xb.destroy()
+    d.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "fc784_256_10_tiles":
         run_tiles(args)
+    elif args.workload == "surrogate128":
+        run_surrogate(args)
     else:
         run_xbar(args)
 

@@ -60,7 +60,11 @@ WORKLOADS = {
                                    precision="fp32_ir",
                                    notes="784-256-10 FC net mapped to 30 ragged tiles, 4096 vectors each"),
     "surrogate128": Workload("surrogate128", 128, 128, 100, (Circuit(1.0, 2.5, 2.5, 10.0),),
-                             notes="per-column MLP surrogate, 128x128 maps"),
+                             notes="per-column MLP surrogate, 128x128 maps: train on 200 maps x 100 vectors, "
+                                   "calibrate on 20 x 100, test on 50 held-out maps x 1000 vectors",
+                             extra={"train_maps": 200, "train_B": 100, "calib_maps": 20, "calib_B": 100,
+                                    "test_maps": 50, "test_B": 1000, "train_seed": 100, "calib_seed": 200,
+                                    "test_seed": 300}),
 }
 
 
