@@ -6,10 +6,11 @@
 // for a panel of 64 input vectors per block.  Each step is D[Mt x 64] = X_j[Mt x Mt] . v[Mt x 64]
 // computed from split TF32 operands (x = x_hi + x_lo, both TF32): with B_hi and B_lo stacked along
 // N, each K step issues A_hi [B_hi | B_lo] and A_lo [B_hi | B_lo] (N = 128) and the epilogue adds
-// the two column halves, so D = (A_hi + A_lo)(B_hi + B_lo) with FP32 accumulation in tensor memory.
-// Dependent accumulations into one TMEM region serialise at ~170 cycles per MMA, so even and odd
-// K steps accumulate into separate regions: 2 row halves x 2 K parities = 4 independent chains., which keeps FP32-level accuracy: a plain TF32
-// product would cost the refinement several extra FP64 residual passes.
+// the two column halves, so D = (A_hi + A_lo)(B_hi + B_lo) with FP32 accumulation in tensor memory,
+// which keeps FP32-level accuracy: a plain TF32 product would cost the refinement several extra
+// FP64 residual passes.  Dependent accumulations into one TMEM region serialise at ~170 cycles
+// per MMA, so even and odd K steps accumulate into separate regions: 2 row halves x 2 K parities
+// = 4 independent chains.
 //
 // Operands.  A = X_j, split and pre-tiled in global memory (sweep_tc_tile_kernel) in the
 // no-swizzle K-major core-matrix order of the MMA (8 rows x 16 bytes per core matrix), chunk by
