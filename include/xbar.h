@@ -86,6 +86,9 @@ typedef struct {
  *   cuda_stream   cudaStream_t all work of this handle runs on (NULL = legacy
  *                 default stream).
  *   out           receives the handle; owns all device memory it allocates.
+ * The conductances are stored at once; the per-column elimination data (bit-line
+ * chain pivots, the blocks C_j of xbar_factor) are formed by the first
+ * xbar_factor, so callers that only need the map (xbar_surrogate_solve) skip them.
  * Errors: XBAR_EINVAL for out-of-range sizes, non-positive or non-finite
  * resistances, negative or non-finite conductances (checked on the host after
  * copying G), or NULL pointers; XBAR_ENOMEM; XBAR_ECUDA.
@@ -143,9 +146,10 @@ typedef enum {
 xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value);
 
 /*
- * xbar_set_conductances -- re-assemble the handle for a new conductance map G
- * (same M, N and resistances; host or device pointer, validated as in
- * xbar_assemble) without reallocating.  The handle becomes unfactored.
+ * xbar_set_conductances -- load a new conductance map G into the handle (same
+ * M, N and resistances; host or device pointer, validated as in xbar_assemble)
+ * without reallocating.  The handle becomes unfactored; as after xbar_assemble,
+ * the column elimination data are formed by the next xbar_factor.
  * Errors: XBAR_EINVAL (NULL handle/G, negative or non-finite G), XBAR_ECUDA.
  */
 xbar_status xbar_set_conductances(xbar_t h, const double* G);

@@ -147,8 +147,8 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Gd, Gh.data(), (size_t)M * N * 8, cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess) {
-    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
-    e = launch_assemble(m, Gd, h->st);
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
+    e = launch_store_g(m, Gd, h->st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cleanup(fail(XBAR_ECUDA, "assembly: %s", cudaGetErrorString(e)));
@@ -229,6 +229,11 @@ static xbar_status do_factor(xbar_t h, bool equilibrate, bool upload) {
 
 xbar_status xbar::factor_handle(xbar_s* h, xbar_precision p, bool upload_params) {
   h->factored = 0;
+  if (!h->assembled) {  // the elimination data of the current conductances
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
+    XB_CUDA(launch_assemble(h->m, h->st));
+    h->assembled = 1;
+  }
   xbar_status s = (p == XBAR_FP64) ? do_factor<double>(h, false, upload_params)
                                    : do_factor<float>(h, true, upload_params);
   if (s != XBAR_OK) return s;
@@ -617,9 +622,10 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
     Gd = (const double*)h->sV.p;
   }
   h->factored = 0;
+  h->assembled = 0;
   {
-    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
-    XB_CUDA(launch_assemble(m, Gd, h->st));
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
+    XB_CUDA(launch_store_g(m, Gd, h->st));
   }
   if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
   return XBAR_OK;

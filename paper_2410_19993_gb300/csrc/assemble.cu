@@ -19,8 +19,16 @@
 
 namespace xbar {
 
-// One thread per bit line j: the chain recurrences of T_j (sequential in i).
-__global__ void asm_columns_kernel(MapDev m, const double* __restrict__ G) {
+// Gc[j][i] = G[i][j] (row-major M x N input), zero in the padding rows i >= M.
+__global__ void asm_gc_kernel(MapDev m, const double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= m.Mp || j >= m.N) return;
+  m.Gc[(size_t)j * m.Mp + i] = i < m.M ? G[(size_t)i * m.N + j] : 0.0;
+}
+
+// One thread per bit line j: the chain recurrences of T_j (sequential in i), from Gc.
+__global__ void asm_columns_kernel(MapDev m) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m.N) return;
   const int M = m.M, N = m.N, Mp = m.Mp;
@@ -37,14 +45,13 @@ __global__ void asm_columns_kernel(MapDev m, const double* __restrict__ G) {
   //           alpha_0 = 0, alpha_i = g_b t / (t + g_b), t = G_{i-1} + alpha_{i-1}
   double alpha = 0.0, gprev = 0.0;
   for (int i = 0; i < M; ++i) {
-    const double g = G[(size_t)i * N + j];
+    const double g = Gc[i];
     if (i > 0) {
       const double t = gprev + alpha;
       alpha = gb * t / (t + gb);
     }
     const double dminus = g + alpha + (i < M - 1 ? gb : go);
     const double inv = 1.0 / dminus;
-    Gc[i] = g;
     dW[i] = g + (j == 0 ? gs : gw) + (j < N - 1 ? gw : 0.0);
     tha[i] = g * inv;
     thc[i] = gb * inv;
@@ -70,7 +77,6 @@ __global__ void asm_columns_kernel(MapDev m, const double* __restrict__ G) {
     gnext = g;
   }
   for (int i = M; i < Mp; ++i) {
-    Gc[i] = 0.0;
     dW[i] = 1.0;
     tha[i] = 0.0;
     thc[i] = 0.0;
@@ -137,8 +143,14 @@ __global__ void asm_coff_kernel(MapDev m) {
   for (int k = M; k < Mp; ++k) C[(size_t)k * Mp + i] = 0.0;
 }
 
-cudaError_t launch_assemble(const MapDev& m, const double* G_dev, cudaStream_t st) {
-  asm_columns_kernel<<<(m.N + 63) / 64, 64, 0, st>>>(m, G_dev);
+cudaError_t launch_store_g(const MapDev& m, const double* G_dev, cudaStream_t st) {
+  dim3 g((m.Mp + 127) / 128, m.N);
+  asm_gc_kernel<<<g, 128, 0, st>>>(m, G_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const MapDev& m, cudaStream_t st) {
+  asm_columns_kernel<<<(m.N + 63) / 64, 64, 0, st>>>(m);
   dim3 g2((m.Mp + 127) / 128, m.N);
   asm_scale_kernel<<<g2, 128, 0, st>>>(m);
   asm_coff_kernel<<<g2, 128, 0, st>>>(m);

@@ -157,7 +157,8 @@ extern "C" xbar_status xbar_batch_run(xbar_batch_t b, xbar_precision p, const in
   XB_CUDA(cudaStreamWaitEvent(b->origin, b->after_user, 0));
   bool same = b->exec && b->sig_prec == (int)p && b->sig_iter == iters && b->sig_tol == tol;
   for (int t = 0; same && t < T; ++t)
-    same = b->sigB[t] == B[t] && b->sigV[t] == (const void*)V[t] && b->sigI[t] == (const void*)I[t];
+    same = b->sigB[t] == B[t] && b->sigV[t] == (const void*)V[t] && b->sigI[t] == (const void*)I[t] &&
+           b->tiles[t]->assembled;  // new conductances: the eager run assembles them outside the graph
   if (!same) {
     destroy_graph(b);
     // eager run: sizes every workspace and uploads the factor parameters

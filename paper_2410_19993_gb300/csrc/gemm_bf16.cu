@@ -12,7 +12,12 @@
 //
 // Epilogues: EPI_STORE (FP32 C, or atomic add for split-K), EPI_BIAS_RELU (H = relu(C + bias) as
 // BF16), EPI_MASK (D = C where mask > 0 else 0, as BF16: the ReLU derivative applied to a
-// back-propagated gradient).
+// back-propagated gradient), EPI_HEAD (h = bf16(relu(C + bias)) reduced at once against the two
+// rows of a 2 x N output layer, partial sums added atomically per row).
+//
+// The A operand can also be generated while staging instead of loaded: relu(P_j + Q_b + bias) for
+// row m = b*gen_N + j, which is the first layer of the surrogate when its input splits into a
+// per-column part (P) and a per-vector part (Q).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -90,6 +95,33 @@ __device__ __forceinline__ void stage(unsigned char* dst, const __nv_bfloat16* P
   }
 }
 
+// stage a [128 rows x 64 k] tile of the generated operand relu(P[m % gN] + Q[m / gN] + bias)
+__device__ __forceinline__ void stage_gen(unsigned char* dst, const GemmBf16Params& p, long r0, long k0, int tid) {
+  for (int q = tid; q < kBM * kBK / 8; q += kThreads) {
+    const int r = q / (kBK / 8), kk = (q % (kBK / 8)) * 8;
+    const long m = r0 + r;
+    alignas(16) __nv_bfloat16 v[8];
+    if (m < p.gen_valid) {
+      const long b = m / p.gen_N, j = m - b * p.gen_N;
+      const float4* P = reinterpret_cast<const float4*>(p.gen_P + j * p.K + k0 + kk);
+      const float4* Q = reinterpret_cast<const float4*>(p.gen_Q + b * p.K + k0 + kk);
+      const float4* c = reinterpret_cast<const float4*>(p.gen_bias + k0 + kk);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 a = P[h], e = Q[h], f = c[h];
+        v[4 * h + 0] = __float2bfloat16_rn(fmaxf(a.x + e.x + f.x, 0.0f));
+        v[4 * h + 1] = __float2bfloat16_rn(fmaxf(a.y + e.y + f.y, 0.0f));
+        v[4 * h + 2] = __float2bfloat16_rn(fmaxf(a.z + e.z + f.z, 0.0f));
+        v[4 * h + 3] = __float2bfloat16_rn(fmaxf(a.w + e.w + f.w, 0.0f));
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __float2bfloat16_rn(0.0f);
+    }
+    *reinterpret_cast<uint4*>(dst + tile_off(r, kk)) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
 }  // namespace g16
 
 __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Params p) {
@@ -130,7 +162,10 @@ __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Par
     if (it >= 2)  // the MMAs that read this buffer two chunks ago are complete
       ok = mbar_spin_bounded(&bar[buf], (unsigned)(((it - 2) >> 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 20);
     if (__syncthreads_or(!ok)) break;
-    stage(At, p.A, p.sAm, p.sAk, m0, (long)kc * kBK, tid);
+    if (p.gen_P)
+      stage_gen(At, p, m0, (long)kc * kBK, tid);
+    else
+      stage(At, p.A, p.sAm, p.sAk, m0, (long)kc * kBK, tid);
     stage(Bt, p.B, p.sBn, p.sBk, n0, (long)kc * kBK, tid);
     fence_proxy_async_smem();
     __syncthreads();
@@ -152,7 +187,25 @@ __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Par
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   // ---- epilogue: warp w owns accumulator rows 32w .. 32w+31 -----------------------------------
-  if (ok && kc1 > kc0) {
+  if (ok && kc1 > kc0 && p.mode == GEMM_EPI_HEAD) {
+    const long row = m0 + warp * 32 + lane;
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int cb = 0; cb < kBN; cb += 32) {
+      float a[32];
+      tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, a);
+      const long col = n0 + cb;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(a[q] + p.bias[col + q], 0.0f)));
+        s0 = fmaf(p.head_W[col + q], h, s0);
+        s1 = fmaf(p.head_W[p.N + col + q], h, s1);
+      }
+    }
+    if (row < p.gen_valid) {
+      atomicAdd(&p.head_out[2 * row], s0);
+      atomicAdd(&p.head_out[2 * row + 1], s1);
+    }
+  } else if (ok && kc1 > kc0) {
     const long row = m0 + warp * 32 + lane;
     for (int cb = 0; cb < kBN; cb += 32) {
       float a[32];
@@ -188,7 +241,10 @@ __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Par
 cudaError_t launch_gemm_bf16(const GemmBf16Params& p, int ksplit, cudaStream_t st) {
   if (p.M % g16::kBM || p.N % g16::kBN || p.K % g16::kBK || p.M <= 0 || p.N <= 0 || p.K <= 0)
     return cudaErrorInvalidValue;
-  if (!(p.sAk == 1 || p.sAm == 1) || !(p.sBk == 1 || p.sBn == 1)) return cudaErrorInvalidValue;
+  if (!p.gen_P && !(p.sAk == 1 || p.sAm == 1)) return cudaErrorInvalidValue;
+  if (!(p.sBk == 1 || p.sBn == 1)) return cudaErrorInvalidValue;
+  if (p.gen_P && (!p.gen_Q || !p.gen_bias || p.gen_N < 1)) return cudaErrorInvalidValue;
+  if (p.mode == GEMM_EPI_HEAD && (!p.head_W || !p.head_out || !p.bias || ksplit != 1)) return cudaErrorInvalidValue;
   const int nks = p.K / g16::kBK;
   if (ksplit < 1) ksplit = 1;
   if (ksplit > nks) ksplit = nks;

@@ -88,6 +88,7 @@ struct xbar_s {
   double R[4] = {0, 0, 0, 0};
   cudaStream_t st = nullptr;
   int dev = 0, nsm = 0;
+  int assembled = 0;  // per-column elimination data formed from Gc (lazily, by the first factor)
   int factored = 0;
   xbar_precision prec = XBAR_FP64;
   xbar::DevArena A;

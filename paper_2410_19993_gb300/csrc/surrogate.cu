@@ -83,9 +83,9 @@ __global__ void prep_rows_kernel(const double* G, long sGi, long sGj, int M, int
     Gt[o] = g;
     acc += g;
     St[o] = (float)(acc * s_scale);
-    const double D = (j == 0 ? gs : gw) + g + gw * delta;
-    wl[o] = 1.0 / D;
-    delta = (g + gw * delta) / D;
+    const double rD = 1.0 / ((j == 0 ? gs : gw) + g + gw * delta);
+    wl[o] = rD;
+    delta = (g + gw * delta) * rD;
   }
 }
 
@@ -97,9 +97,9 @@ __global__ void prep_cols_kernel(const double* Gt, int M, int N, double gb, doub
   double* z = xg + (long)j * M;
   double eps = 0.0;
   for (int i = 0; i < M; ++i) {
-    const double E = g[i] + gb * eps + (i < M - 1 ? gb : go);
-    e[i] = 1.0 / E;
-    eps = (g[i] + gb * eps) / E;
+    const double rE = 1.0 / (g[i] + gb * eps + (i < M - 1 ? gb : go));
+    e[i] = rE;
+    eps = (g[i] + gb * eps) * rE;
   }
   double x = e[M - 1];  // unit current at the bottom node: s_i = 0 above it
   for (int i = M - 1; i >= 0; --i) {
@@ -110,23 +110,61 @@ __global__ void prep_cols_kernel(const double* Gt, int M, int N, double gb, doub
 
 // Field of unit-input responses for inputs k0 .. k0+K-1: F[(kk*N + j)*M + i] is node (i, j) for
 // input k = k0 + kk.  Word-line pass, one thread per (kk, i): w_i = (L_i + diag G_i)^-1
-// (G_i o u_i + g_s [i == k] e_0), u = 0 on the first pass, written over u.
-__global__ void wl_pass_kernel(const double* Gt, const double* wl, double* F, int K, int k0, int M, int N, double gs,
-                               double gw, int first) {
+// (G_i o u_i + g_s [i == k] e_0), u = 0 on the first pass (where only row k is non-zero), written
+// over u.  The chains are sequential; loads are issued 8 steps ahead of the arithmetic.
+constexpr int kU = 8;
+__global__ void wl_pass_kernel(const double* __restrict__ Gt, const double* __restrict__ wl, double* __restrict__ F,
+                               int K, int k0, int M, int N, double gs, double gw, int first) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= (long)K * M) return;
   const int kk = (int)(t / M), i = (int)(t - (long)kk * M);
   double* f = F + (long)kk * N * M + i;  // node (i, j) at f[j*M]
+  const bool src = (i == k0 + kk);
+  if (first && !src) {
+    for (int j = 0; j < N; ++j) f[(long)j * M] = 0.0;
+    return;
+  }
   double tn = 0.0;
-  for (int j = N - 1; j >= 0; --j) {
+  int j = N - 1;
+  for (; j >= kU - 1; j -= kU) {  // back pass: t_j = (r_j + g_w t_{j+1}) / D_j
+    double r[kU], d[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long o = (long)(j - u) * M;
+      r[u] = first ? 0.0 : Gt[o + i] * f[o];
+      d[u] = wl[o + i];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (src && j - u == 0) r[u] += gs;
+      tn = (r[u] + gw * tn) * d[u];
+      f[(long)(j - u) * M] = tn;
+    }
+  }
+  for (; j >= 0; --j) {
     const long o = (long)j * M;
     double r = first ? 0.0 : Gt[o + i] * f[o];
-    if (j == 0 && i == k0 + kk) r += gs;
+    if (src && j == 0) r += gs;
     tn = (r + gw * tn) * wl[o + i];
     f[o] = tn;
   }
-  double w = f[0];
-  for (int j = 1; j < N; ++j) {
+  double w = f[0];  // forward: w_j = (g_w / D_j) w_{j-1} + t_j
+  j = 1;
+  for (; j + kU <= N; j += kU) {
+    double tv[kU], d[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long o = (long)(j + u) * M;
+      tv[u] = f[o];
+      d[u] = wl[o + i];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      w = gw * d[u] * w + tv[u];
+      f[(long)(j + u) * M] = w;
+    }
+  }
+  for (; j < N; ++j) {
     const long o = (long)j * M;
     w = gw * wl[o + i] * w + f[o];
     f[o] = w;
@@ -134,7 +172,8 @@ __global__ void wl_pass_kernel(const double* Gt, const double* wl, double* F, in
 }
 
 // Bit-line pass, one thread per (kk, j): u_j = (K_j + diag G_j)^-1 (G_j o w_j), written over w.
-__global__ void bl_pass_kernel(const double* Gt, const double* bl, double* F, int K, int M, int N, double gb) {
+__global__ void bl_pass_kernel(const double* __restrict__ Gt, const double* __restrict__ bl, double* __restrict__ F,
+                               int K, int M, int N, double gb) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= (long)K * N) return;
   const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
@@ -142,27 +181,118 @@ __global__ void bl_pass_kernel(const double* Gt, const double* bl, double* F, in
   const double* g = Gt + (long)j * M;
   const double* e = bl + (long)j * M;
   double sp = 0.0;
-  for (int i = 0; i < M; ++i) {
+  int i = 0;
+  for (; i + kU <= M; i += kU) {  // forward: s_i = (r_i + g_b s_{i-1}) / E_i
+    double r[kU], d[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      r[u] = g[i + u] * f[i + u];
+      d[u] = e[i + u];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      sp = (r[u] + gb * sp) * d[u];
+      f[i + u] = sp;
+    }
+  }
+  for (; i < M; ++i) {
     sp = (g[i] * f[i] + gb * sp) * e[i];
     f[i] = sp;
   }
-  double x = f[M - 1];
-  for (int i = M - 2; i >= 0; --i) {
+  double x = f[M - 1];  // back: x_i = (g_b / E_i) x_{i+1} + s_i
+  i = M - 2;
+  for (; i >= kU - 1; i -= kU) {
+    double sv[kU], d[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      sv[u] = f[i - u];
+      d[u] = e[i - u];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      x = gb * d[u] * x + sv[u];
+      f[i - u] = x;
+    }
+  }
+  for (; i >= 0; --i) {
     x = gb * e[i] * x + f[i];
     f[i] = x;
   }
 }
 
 // Sense currents of the last word-line pass: T[j*M + k] = sum_i xg(i, j) w(i, j; k).
-__global__ void line_transfer_kernel(const double* xg, const double* F, int K, int k0, int M, int N, double* T) {
+__global__ void line_transfer_kernel(const double* __restrict__ xg, const double* __restrict__ F, int K, int k0, int M,
+                                     int N, double* __restrict__ T) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= (long)K * N) return;
   const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
   const double* f = F + ((long)kk * N + j) * M;
   const double* z = xg + (long)j * M;
-  double acc = 0.0;
-  for (int i = 0; i < M; ++i) acc += z[i] * f[i];
-  T[(long)j * M + k0 + kk] = acc;
+  double acc[kU] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int i = 0;
+  for (; i + kU <= M; i += kU) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) acc[u] += z[i + u] * f[i + u];
+  }
+  for (; i < M; ++i) acc[0] += z[i] * f[i];
+  double a = 0.0;
+#pragma unroll
+  for (int u = 0; u < kU; ++u) a += acc[u];
+  T[(long)j * M + k0 + kk] = a;
+}
+
+// ---- inference inputs: the first layer splits into a per-column and a per-vector product ------
+// XGS[j] = [G(:,j)/g_scale, 0, S(:,j)/(N g_scale), 0 pad] for j < N (zero rows up to Npad);
+// XV[b]  = [0, V_b/v_scale, 0, 0 pad] for b < B (zero rows up to Bpad).  Then
+// X(b, j) W1^T = XGS[j] W1^T + XV[b] W1^T.
+__global__ void infer_xgs_kernel(const double* Gt, const float* St, int M, int N, int Npad, int Fp, double inv_gs,
+                                 __nv_bfloat16* XGS) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)Npad * Fp) return;
+  const int j = (int)(t / Fp), f = (int)(t - (long)j * Fp);
+  float x = 0.0f;
+  if (j < N) {
+    if (f < M) x = (float)(Gt[(long)j * M + f] * inv_gs);
+    else if (f >= 2 * M && f < 3 * M) x = St[(long)j * M + f - 2 * M];
+  }
+  XGS[t] = __float2bfloat16_rn(x);
+}
+
+__global__ void infer_xv_kernel(const double* V, int M, int B, int Bpad, int Fp, double inv_vs, __nv_bfloat16* XV) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)Bpad * Fp) return;
+  const int b = (int)(t / Fp), f = (int)(t - (long)b * Fp);
+  float x = 0.0f;
+  if (b < B && f >= M && f < 2 * M) x = (float)(V[(long)b * M + f - M] * inv_vs);
+  XV[t] = __float2bfloat16_rn(x);
+}
+
+// FP32 copies in [M][N] layout (row i contiguous over columns j) of G and T_line
+__global__ void infer_gt32_kernel(const double* Gt, const double* Tl, int M, int N, float* G32, float* T32) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)M * N) return;
+  const int i = (int)(t / N), j = (int)(t - (long)i * N);
+  G32[t] = (float)Gt[(long)j * M + i];
+  T32[t] = (float)Tl[(long)j * M + i];
+}
+
+// I_ideal[b][j] = V_b . G(:, j), I_line[b][j] = V_b . T_line(:, j), FP32 accumulation (their
+// relative error, ~1e-7, is far below the network's); one block per input vector b
+__global__ void infer_currents_kernel(const double* V, const float* G32, const float* T32, int M, int N,
+                                      double* Iid, double* Iln) {
+  extern __shared__ float vs[];
+  const int b = blockIdx.x;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) vs[i] = (float)V[(long)b * M + i];
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float a = 0.0f, c = 0.0f;
+    for (int i = 0; i < M; ++i) {
+      a = fmaf(vs[i], G32[(long)i * N + j], a);
+      c = fmaf(vs[i], T32[(long)i * N + j], c);
+    }
+    Iid[(long)b * N + j] = a;
+    Iln[(long)b * N + j] = c;
+  }
 }
 
 // one block (128 threads) per row r = b*N + j: features, ideal and line-model currents, and
@@ -214,10 +344,9 @@ __global__ void feature_kernel(const double* Gt, const float* St, const double* 
 }
 
 // Layer 3, loss and back-propagation to dZ2; one warp per row, lane l owns hidden units 8l..8l+7.
-// train: accumulates dW3, db3 and the two loss sums; predict: writes out[r] = (out0, out1).
+// Accumulates dW3, db3 and the two loss sums.
 __global__ void head_kernel(const __nv_bfloat16* H2, const float* W3, const float* b3, const float* y, long rows,
-                            long valid, int train, float inv_rows, float* out, __nv_bfloat16* dZ2, float* dW3,
-                            float* db3, double* loss) {
+                            long valid, float inv_rows, __nv_bfloat16* dZ2, float* dW3, float* db3, double* loss) {
   const int lane = threadIdx.x & 31;
   const long warp0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
@@ -244,13 +373,6 @@ __global__ void head_kernel(const __nv_bfloat16* H2, const float* W3, const floa
       a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     }
     const float o0 = a0 + b3[0], o1 = a1 + b3[1];
-    if (!train) {
-      if (lane == 0 && r < valid) {
-        out[2 * r] = o0;
-        out[2 * r + 1] = o1;
-      }
-      continue;
-    }
     float d0 = 0.0f, d1 = 0.0f;
     if (r < valid) {
       const float e = o0 - y[r];
@@ -271,7 +393,6 @@ __global__ void head_kernel(const __nv_bfloat16* H2, const float* W3, const floa
     gb0 += d0;
     gb1 += d1;
   }
-  if (!train) return;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     atomicAdd(&dW3[lane * 8 + q], g0[q]);
@@ -322,13 +443,15 @@ __global__ void f32_to_bf16_rows_kernel(const float* X, long rows, int F, int Fp
 
 // prediction: I = I_line + I_ideal (mu + sigma n0), relative error estimate
 // c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when any entry of vector b is above the bound
-__global__ void finalize_kernel(const float* out, const double* Iid, const double* Iln, long rows, double mu,
-                                double sigma, double cal, double bound, double* I, double* est, int* flag, int N) {
+__global__ void finalize_kernel(const float* out, const float* b3, const double* Iid, const double* Iln, long rows,
+                                double mu, double sigma, double cal, double bound, double* I, double* est, int* flag,
+                                int N) {
   const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const double ii = Iid[r];
-  const double Ir = Iln[r] + ii * (mu + sigma * (double)out[2 * r]);
-  const double e = cal * sigma * exp((double)out[2 * r + 1]) * fabs(ii) / fmax(fabs(Ir), 1e-300);
+  const double n0 = (double)(out[2 * r] + b3[0]), n1 = (double)(out[2 * r + 1] + b3[1]);
+  const double Ir = Iln[r] + ii * (mu + sigma * n0);
+  const double e = cal * sigma * exp(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
   I[r] = Ir;
   if (est) est[r] = e;
   if (flag && !(e <= bound)) flag[r / N] = 1;
@@ -381,6 +504,8 @@ struct xbar_surrogate_s {
   // per-map line model and feature columns: [N][M]
   int passes = 1;
   Buf Gt, St, Tl, wl, bl, xg, field;
+  // inference: split first layer and FP32 copies for the current contractions
+  Buf xgs, xv, Pm, Qm, g32, t32;
   // training set
   Buf Xall, yall;
 };
@@ -507,10 +632,9 @@ extern "C" xbar_status xbar_surrogate_scaling(xbar_surrogate_t s, const double* 
   return XBAR_OK;
 }
 
-// forward (and with train != 0 backward) on rows [0, rows) of the workspace feature matrix X;
+// forward and backward (training) on rows [0, rows) of the feature matrix X;
 // `valid` rows are real (the rest are zero padding up to a multiple of 128)
-static xbar_status fwd_bwd(xbar_surrogate_t s, const __nv_bfloat16* X, long rows, long valid, const float* y,
-                           int train) {
+static xbar_status fwd_bwd(xbar_surrogate_t s, const __nv_bfloat16* X, long rows, long valid, const float* y) {
   const int Fp = s->Fp;
   GemmBf16Params g;
   memset(&g, 0, sizeof(g));
@@ -527,16 +651,10 @@ static xbar_status fwd_bwd(xbar_surrogate_t s, const __nv_bfloat16* X, long rows
   g.bias = s->P + s->ob2; g.out = (__nv_bfloat16*)s->H2.p;
   XB_CUDA(launch_gemm_bf16(g, 1, s->st));
   const int hb = (int)std::min<long>(4096, (rows + 7) / 8);
-  if (!train) {
-    head_kernel<<<hb, 256, 0, s->st>>>((const __nv_bfloat16*)s->H2.p, s->P + s->oW3, s->P + s->ob3, nullptr, rows,
-                                       valid, 0, 0.0f, (float*)s->out.p, nullptr, nullptr, nullptr, nullptr);
-    XB_CUDA(cudaGetLastError());
-    return XBAR_OK;
-  }
   XB_CUDA(cudaMemsetAsync(s->Gr, 0, s->np * 4, s->st));
-  head_kernel<<<hb, 256, 0, s->st>>>((const __nv_bfloat16*)s->H2.p, s->P + s->oW3, s->P + s->ob3, y, rows, valid, 1,
-                                     1.0f / (float)valid, nullptr, (__nv_bfloat16*)s->dZ2.p, s->Gr + s->oW3,
-                                     s->Gr + s->ob3, s->loss);
+  head_kernel<<<hb, 256, 0, s->st>>>((const __nv_bfloat16*)s->H2.p, s->P + s->oW3, s->P + s->ob3, y, rows, valid,
+                                     1.0f / (float)valid, (__nv_bfloat16*)s->dZ2.p, s->Gr + s->oW3, s->Gr + s->ob3,
+                                     s->loss);
   XB_CUDA(cudaGetLastError());
   const int ks = (int)std::max<long>(1, std::min<long>(64, rows / 1024));
   // dW2 = dZ2^T H1
@@ -591,7 +709,7 @@ extern "C" xbar_status xbar_surrogate_grad(xbar_surrogate_t s, int R, const floa
   f32_to_bf16_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s->st>>>(dXf, R, s->F, s->Fp,
                                                                            (__nv_bfloat16*)s->X.p);
   XB_CUDA(cudaMemsetAsync(s->loss, 0, 16, s->st));
-  xbar_status st = fwd_bwd(s, (const __nv_bfloat16*)s->X.p, rows, R, dy, 1);
+  xbar_status st = fwd_bwd(s, (const __nv_bfloat16*)s->X.p, rows, R, dy);
   double l[2] = {0, 0};
   unsigned dst = 0;
   if (st == XBAR_OK) {
@@ -611,10 +729,8 @@ extern "C" xbar_status xbar_surrogate_grad(xbar_surrogate_t s, int R, const floa
   return st;
 }
 
-// line model and feature columns of one map (G(i, j) = G[i*sGi + j*sGj], device), then features,
-// ideal and line-model currents (and targets when Iex != NULL) of its B vectors into X, q, Iid, Iln
-static xbar_status build_features(xbar_surrogate_t s, const double* G, long sGi, long sGj, int B, const double* V,
-                                  const double* Iex, __nv_bfloat16* X, float* q, double* Iid, double* Iln) {
+// line model and feature columns of one map (G(i, j) = G[i*sGi + j*sGj], device): Gt, St, Tl
+static xbar_status map_prep(xbar_surrogate_t s, const double* G, long sGi, long sGj) {
   const int M = s->M, N = s->N;
   const size_t mn = (size_t)M * N;
   // inputs per chunk of the response field: at most 256 MiB of it
@@ -641,9 +757,19 @@ static xbar_status build_features(xbar_surrogate_t s, const double* G, long sGi,
     }
     line_transfer_kernel<<<gn, 128, 0, s->st>>>((const double*)s->xg.p, F, Kc, k0, M, N, (double*)s->Tl.p);
   }
-  feature_kernel<<<(unsigned)((long)B * N), 128, 0, s->st>>>(Gt, (const float*)s->St.p, (const double*)s->Tl.p, V,
-                                                             Iex, M, N, B, s->Fp, 1.0 / s->gs, 1.0 / s->vs, X, q, Iid,
-                                                             Iln);
+  XB_CUDA(cudaGetLastError());
+  return XBAR_OK;
+}
+
+// training rows of one map: features, ideal and line-model currents and (when Iex != NULL) the
+// targets of its B vectors into X, q, Iid, Iln
+static xbar_status build_features(xbar_surrogate_t s, const double* G, long sGi, long sGj, int B, const double* V,
+                                  const double* Iex, __nv_bfloat16* X, float* q, double* Iid, double* Iln) {
+  xbar_status st = map_prep(s, G, sGi, sGj);
+  if (st != XBAR_OK) return st;
+  feature_kernel<<<(unsigned)((long)B * s->N), 128, 0, s->st>>>((const double*)s->Gt.p, (const float*)s->St.p,
+                                                                (const double*)s->Tl.p, V, Iex, s->M, s->N, B, s->Fp,
+                                                                1.0 / s->gs, 1.0 / s->vs, X, q, Iid, Iln);
   XB_CUDA(cudaGetLastError());
   return XBAR_OK;
 }
@@ -735,7 +861,7 @@ extern "C" xbar_status xbar_surrogate_train(xbar_surrogate_t s, int n_maps, cons
       const long valid = std::min<long>(batch_rows, total - start);
       if (valid <= 0) continue;
       xbar_status st = fwd_bwd(s, (const __nv_bfloat16*)s->Xall.p + start * s->Fp, batch_rows, valid,
-                               (const float*)s->yall.p + start, 1);
+                               (const float*)s->yall.p + start);
       if (st != XBAR_OK) return st;
       ++s->adam_t;
       const float c1 = 1.0f - powf(b1, (float)s->adam_t), c2 = 1.0f - powf(b2, (float)s->adam_t);
@@ -757,19 +883,78 @@ extern "C" xbar_status xbar_surrogate_train(xbar_surrogate_t s, int n_maps, cons
   return XBAR_OK;
 }
 
-// predict one map held in device memory (G(i,j) = G[i*sGi + j*sGj]); I, est, flag on the device
+// predict one map held in device memory (G(i,j) = G[i*sGi + j*sGj]); I, est, flag on the device.
+// Inference uses the split first layer: P = XGS W1^T (one row per column j), Q = XV W1^T (one row
+// per vector b); the second product generates its operand relu(P_j + Q_b + b1) while staging and
+// reduces relu(. + b2) against W3 in its epilogue, so no per-row feature or activation matrix is
+// ever written.
 static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, long sGj, int B, const double* V,
                                double* I, double* est, int* flag, double bound) {
-  const long rows = (long)B * s->N, padded = round_up_l(rows, 128);
-  if (ensure_rows(s, padded) != XBAR_OK) return XBAR_ENOMEM;
-  xbar_status st = build_features(s, G, sGi, sGj, B, V, nullptr, (__nv_bfloat16*)s->X.p, nullptr,
-                                  (double*)s->Iid.p, (double*)s->Iln.p);
+  const int M = s->M, N = s->N, Fp = s->Fp;
+  const long rows = (long)B * N, padded = round_up_l(rows, 128);
+  const long Npad = round_up_l(N, 128), Bpad = round_up_l(B, 128);
+  xbar_status st = map_prep(s, G, sGi, sGj);
   if (st != XBAR_OK) return st;
-  st = fwd_bwd(s, (const __nv_bfloat16*)s->X.p, padded, rows, nullptr, 0);
-  if (st != XBAR_OK) return st;
-  finalize_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s->st>>>((const float*)s->out.p, (const double*)s->Iid.p,
-                                                                      (const double*)s->Iln.p, rows, s->mu, s->sigma,
-                                                                      s->cal, bound, I, est, flag, s->N);
+  XB_CUDA(ensure(s->A, s->Iid, (size_t)rows * 8));
+  XB_CUDA(ensure(s->A, s->Iln, (size_t)rows * 8));
+  XB_CUDA(ensure(s->A, s->out, (size_t)rows * 8));
+  XB_CUDA(ensure(s->A, s->xgs, (size_t)Npad * Fp * 2));
+  XB_CUDA(ensure(s->A, s->xv, (size_t)Bpad * Fp * 2));
+  XB_CUDA(ensure(s->A, s->Pm, (size_t)Npad * kH * 4));
+  XB_CUDA(ensure(s->A, s->Qm, (size_t)Bpad * kH * 4));
+  XB_CUDA(ensure(s->A, s->g32, (size_t)M * N * 4));
+  XB_CUDA(ensure(s->A, s->t32, (size_t)M * N * 4));
+  infer_xgs_kernel<<<(unsigned)((Npad * Fp + 255) / 256), 256, 0, s->st>>>(
+      (const double*)s->Gt.p, (const float*)s->St.p, M, N, (int)Npad, Fp, 1.0 / s->gs, (__nv_bfloat16*)s->xgs.p);
+  infer_xv_kernel<<<(unsigned)((Bpad * Fp + 255) / 256), 256, 0, s->st>>>(V, M, B, (int)Bpad, Fp, 1.0 / s->vs,
+                                                                           (__nv_bfloat16*)s->xv.p);
+  infer_gt32_kernel<<<(unsigned)(((long)M * N + 255) / 256), 256, 0, s->st>>>(
+      (const double*)s->Gt.p, (const double*)s->Tl.p, M, N, (float*)s->g32.p, (float*)s->t32.p);
+  infer_currents_kernel<<<B, 128, M * sizeof(float), s->st>>>(V, (const float*)s->g32.p, (const float*)s->t32.p, M, N,
+                                                              (double*)s->Iid.p, (double*)s->Iln.p);
+  XB_CUDA(cudaGetLastError());
+  GemmBf16Params g;
+  memset(&g, 0, sizeof(g));
+  g.status = s->status;
+  g.N = kH;
+  g.K = Fp;
+  g.sAm = Fp;
+  g.sAk = 1;
+  g.B = s->W1b;
+  g.sBn = Fp;
+  g.sBk = 1;
+  g.mode = GEMM_EPI_STORE;
+  g.ldc = kH;
+  g.M = (int)Npad;
+  g.A = (const __nv_bfloat16*)s->xgs.p;
+  g.C = (float*)s->Pm.p;
+  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
+  g.M = (int)Bpad;
+  g.A = (const __nv_bfloat16*)s->xv.p;
+  g.C = (float*)s->Qm.p;
+  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
+  XB_CUDA(cudaMemsetAsync(s->out.p, 0, (size_t)rows * 8, s->st));
+  memset(&g, 0, sizeof(g));
+  g.status = s->status;
+  g.M = (int)padded;
+  g.N = kH;
+  g.K = kH;
+  g.gen_P = (const float*)s->Pm.p;
+  g.gen_Q = (const float*)s->Qm.p;
+  g.gen_bias = s->P + s->ob1;
+  g.gen_N = N;
+  g.gen_valid = rows;
+  g.B = s->W2b;
+  g.sBn = kH;
+  g.sBk = 1;
+  g.mode = GEMM_EPI_HEAD;
+  g.bias = s->P + s->ob2;
+  g.head_W = s->P + s->oW3;
+  g.head_out = (float*)s->out.p;
+  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
+  finalize_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s->st>>>(
+      (const float*)s->out.p, s->P + s->ob3, (const double*)s->Iid.p, (const double*)s->Iln.p, rows, s->mu, s->sigma,
+      s->cal, bound, I, est, flag, N);
   XB_CUDA(cudaGetLastError());
   return XBAR_OK;
 }
