@@ -75,50 +75,90 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k) {
   return (uint32_t)(k >> 3) * kLBO + (uint32_t)(row >> 3) * 128 + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 7) * 2;
 }
 
-// stage a [128 rows x 64 k] tile of op(r, k) = P[(r0 + r)*sR + (k0 + k)*sK] into `dst`
-__device__ __forceinline__ void stage(unsigned char* dst, const __nv_bfloat16* P, long sR, long sK, long r0,
-                                      long k0, int tid) {
-  if (sK == 1) {  // k contiguous: 16-byte loads of 8 k values of one row
-    for (int q = tid; q < kBM * kBK / 8; q += kThreads) {
-      const int r = q / (kBK / 8), kk = (q % (kBK / 8)) * 8;
-      const uint4 v = *reinterpret_cast<const uint4*>(P + (r0 + r) * sR + (k0 + kk));
-      *reinterpret_cast<uint4*>(dst + tile_off(r, kk)) = v;
-    }
-  } else {        // rows contiguous (sR == 1): 16-byte loads of 8 rows at one k, scattered
-    for (int q = tid; q < kBM * kBK / 8; q += kThreads) {
-      const int kk = q / (kBM / 8), r = (q % (kBM / 8)) * 8;
-      const uint4 v = *reinterpret_cast<const uint4*>(P + (r0 + r) + (k0 + kk) * sK);
-      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+// Staging a [128 rows x 64 k] tile into the core-matrix layout.  A 16-byte store holds 8 k values
+// of one row; its bank group is set by the row (r & 7), so a warp's stores are conflict-free when
+// its 32 threads store 32 consecutive rows at one k group.  Each thread issues all of its loads
+// before its shared-memory stores, so one chunk costs one memory latency.
+static_assert(kThreads == kBM, "one thread per tile row");
+constexpr int kKG = kBK / 8;  // k groups of 8 per chunk
+
+// rotate the 8 entries of v left by rot (0..7) without dynamic register indexing
+__device__ __forceinline__ void rotate8(uint4 (&v)[8], int rot) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) *reinterpret_cast<__nv_bfloat16*>(dst + tile_off(r + u, kk)) = e[u];
+  for (int b = 0; b < 3; ++b) {
+    const int sh = 1 << b;
+    if (rot & sh) {
+      uint4 t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = v[(u + sh) & 7];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = t[u];
     }
   }
 }
 
-// stage a [128 rows x 64 k] tile of the generated operand relu(P[m % gN] + Q[m / gN] + bias)
-__device__ __forceinline__ void stage_gen(unsigned char* dst, const GemmBf16Params& p, long r0, long k0, int tid) {
-  for (int q = tid; q < kBM * kBK / 8; q += kThreads) {
-    const int r = q / (kBK / 8), kk = (q % (kBK / 8)) * 8;
-    const long m = r0 + r;
-    alignas(16) __nv_bfloat16 v[8];
-    if (m < p.gen_valid) {
-      const long b = m / p.gen_N, j = m - b * p.gen_N;
-      const float4* P = reinterpret_cast<const float4*>(p.gen_P + j * p.K + k0 + kk);
-      const float4* Q = reinterpret_cast<const float4*>(p.gen_Q + b * p.K + k0 + kk);
-      const float4* c = reinterpret_cast<const float4*>(p.gen_bias + k0 + kk);
+// op(r, k) = P[(r0 + r)*sR + (k0 + k)*sK]
+__device__ __forceinline__ void stage(unsigned char* dst, const __nv_bfloat16* P, long sR, long sK, long r0,
+                                      long k0, int tid) {
+  uint4 v[8];
+  if (sK == 1) {  // k contiguous: thread = row, eight 16-byte loads along its row
+    const __nv_bfloat16* src = P + (r0 + tid) * sR + k0;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float4 a = P[h], e = Q[h], f = c[h];
-        v[4 * h + 0] = __float2bfloat16_rn(fmaxf(a.x + e.x + f.x, 0.0f));
-        v[4 * h + 1] = __float2bfloat16_rn(fmaxf(a.y + e.y + f.y, 0.0f));
-        v[4 * h + 2] = __float2bfloat16_rn(fmaxf(a.z + e.z + f.z, 0.0f));
-        v[4 * h + 3] = __float2bfloat16_rn(fmaxf(a.w + e.w + f.w, 0.0f));
-      }
-    } else {
+    for (int g = 0; g < kKG; ++g) v[g] = *reinterpret_cast<const uint4*>(src + g * 8);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __float2bfloat16_rn(0.0f);
+    for (int g = 0; g < kKG; ++g) *reinterpret_cast<uint4*>(dst + tile_off(tid, g * 8)) = v[g];
+  } else {        // rows contiguous (sR == 1): thread = 8 rows x 8 k block, transposed in registers
+    const int rg = tid & 15, kg = tid >> 4;  // row group (16) x k group (8) = 128 blocks
+    const __nv_bfloat16* src = P + (r0 + rg * 8) + (k0 + kg * 8) * sK;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = *reinterpret_cast<const uint4*>(src + e * sK);  // 8 rows at k = e
+    uint4 o[8];
+    const __nv_bfloat16* in = reinterpret_cast<const __nv_bfloat16*>(v);
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(o);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) out[u * 8 + e] = in[e * 8 + u];
+    // store row (s + rg) & 7 at step s: a warp's 32 stores then cover all eight bank groups
+    rotate8(o, rg & 7);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int u = (s + rg) & 7;
+      *reinterpret_cast<uint4*>(dst + tile_off(rg * 8 + u, kg * 8)) = o[s];
     }
-    *reinterpret_cast<uint4*>(dst + tile_off(r, kk)) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+// stage a [128 rows x 64 k] tile of the generated operand relu(P[m % gN] + Q[m / gN] + bias),
+// thread = row, in two halves of the chunk (register budget)
+__device__ __forceinline__ void stage_gen(unsigned char* dst, const GemmBf16Params& p, long r0, long k0, int tid) {
+  const long m = r0 + tid;
+  const bool ok = m < p.gen_valid;
+  const long b = ok ? m / p.gen_N : 0, j = ok ? m - b * p.gen_N : 0;
+  const float4* P = reinterpret_cast<const float4*>(p.gen_P + j * p.K + k0);
+  const float4* Q = reinterpret_cast<const float4*>(p.gen_Q + b * p.K + k0);
+  const float4* C = reinterpret_cast<const float4*>(p.gen_bias + k0);
+  constexpr int kH2 = kKG / 2;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float4 pa[2 * kH2], qa[2 * kH2];
+#pragma unroll
+    for (int g = 0; g < 2 * kH2; ++g) {
+      pa[g] = P[h * 2 * kH2 + g];
+      qa[g] = Q[h * 2 * kH2 + g];
+    }
+#pragma unroll
+    for (int g = 0; g < kH2; ++g) {
+      const int kg = h * kH2 + g;
+      const float4 a0 = pa[2 * g], a1 = pa[2 * g + 1], e0 = qa[2 * g], e1 = qa[2 * g + 1];
+      const float4 c0 = C[2 * kg], c1 = C[2 * kg + 1];
+      const float z[8] = {a0.x + e0.x + c0.x, a0.y + e0.y + c0.y, a0.z + e0.z + c0.z, a0.w + e0.w + c0.w,
+                          a1.x + e1.x + c1.x, a1.y + e1.y + c1.y, a1.z + e1.z + c1.z, a1.w + e1.w + c1.w};
+      alignas(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(ok ? fmaxf(z[e], 0.0f) : 0.0f);
+      *reinterpret_cast<uint4*>(dst + tile_off(tid, kg * 8)) = *reinterpret_cast<const uint4*>(v);
+    }
   }
 }
 
@@ -243,6 +283,9 @@ cudaError_t launch_gemm_bf16(const GemmBf16Params& p, int ksplit, cudaStream_t s
     return cudaErrorInvalidValue;
   if (!p.gen_P && !(p.sAk == 1 || p.sAm == 1)) return cudaErrorInvalidValue;
   if (!(p.sBk == 1 || p.sBn == 1)) return cudaErrorInvalidValue;
+  // 16-byte staging loads: the non-unit stride of each loaded operand is a multiple of 8 elements
+  if (!p.gen_P && ((p.sAk == 1 ? p.sAm : p.sAk) % 8)) return cudaErrorInvalidValue;
+  if ((p.sBk == 1 ? p.sBn : p.sBk) % 8) return cudaErrorInvalidValue;
   if (p.gen_P && (!p.gen_Q || !p.gen_bias || p.gen_N < 1)) return cudaErrorInvalidValue;
   if (p.mode == GEMM_EPI_HEAD && (!p.head_W || !p.head_out || !p.bias || ksplit != 1)) return cudaErrorInvalidValue;
   const int nks = p.K / g16::kBK;

@@ -52,6 +52,8 @@ using namespace xbar;
 namespace {
 
 constexpr int kH = 256;          // hidden width
+constexpr size_t kLineSmemMax = 220 * 1024;  // line model kept in shared memory up to this size
+constexpr size_t kPrepSmemMax = 220 * 1024;  // chain factoring: 32 lines per block in shared memory
 constexpr float kLambda = 0.1f;  // weight of the error head
 constexpr float kEps = 1e-6f;    // floor of the error-head target |out0 - y|
 
@@ -70,175 +72,271 @@ constexpr float kEps = 1e-6f;    // floor of the error-head target |out0 - y|
 //     eps_i = (G(i, j) + g_b eps_{i-1}) / E_i;
 //   solve (K_j + diag G_j) x = r:  s_i = (r_i + g_b s_{i-1}) / E_i (s_{-1} = 0),
 //                                  x_{M-1} = s_{M-1},  x_i = (g_b / E_i) x_{i+1} + s_i.
-// One thread per line, FP64.  Outputs in [N][M] layout (element (i, j) at j*M + i):
-//   Gt = G, St = S / (N g_scale), wl = 1/D, bl = 1/E, xg = g_o z G with z = (K_j + diag G_j)^-1 e_{M-1}.
-__global__ void prep_rows_kernel(const double* G, long sGi, long sGj, int M, int N, double gs, double gw,
-                                 double s_scale, double* Gt, float* St, double* wl) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  double acc = 0.0, delta = 0.0;
-  for (int j = N - 1; j >= 0; --j) {
-    const double g = G[i * sGi + j * sGj];
-    const long o = (long)j * M + i;
-    Gt[o] = g;
-    acc += g;
-    St[o] = (float)(acc * s_scale);
-    const double rD = 1.0 / ((j == 0 ? gs : gw) + g + gw * delta);
-    wl[o] = rD;
-    delta = (g + gw * delta) * rD;
-  }
-}
-
-__global__ void prep_cols_kernel(const double* Gt, int M, int N, double gb, double go, double* bl, double* xg) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  const double* g = Gt + (long)j * M;
-  double* e = bl + (long)j * M;
-  double* z = xg + (long)j * M;
-  double eps = 0.0;
-  for (int i = 0; i < M; ++i) {
-    const double rE = 1.0 / (g[i] + gb * eps + (i < M - 1 ? gb : go));
-    e[i] = rE;
-    eps = (g[i] + gb * eps) * rE;
-  }
-  double x = e[M - 1];  // unit current at the bottom node: s_i = 0 above it
-  for (int i = M - 1; i >= 0; --i) {
-    z[i] = go * x * g[i];
-    if (i > 0) x *= gb * e[i - 1];
-  }
-}
-
-// Field of unit-input responses for inputs k0 .. k0+K-1: F[(kk*N + j)*M + i] is node (i, j) for
-// input k = k0 + kk.  Word-line pass, one thread per (kk, i): w_i = (L_i + diag G_i)^-1
-// (G_i o u_i + g_s [i == k] e_0), u = 0 on the first pass (where only row k is non-zero), written
-// over u.  The chains are sequential; loads are issued 8 steps ahead of the arithmetic.
+// The ratio recurrences are Moebius maps with positive coefficients, so each ratio is carried as
+// a pair (delta = a / b): the pair obeys a division-free positive linear recurrence (rescaled by
+// powers of two every kU steps, which is exact), and the reciprocal pivots 1/D_j = b_j / b_{j-1}
+// come off the sequential path.  One thread per line.
+//
+// Precision: the line model is the physical estimate the network corrects, whose own error is
+// ~1e-4, so its chains run in FP32 (FP64 is 1/64 of the FP32 rate on this part); every step is a
+// sum of positive terms, so the relative error stays at the level of the chain length times the
+// FP32 unit roundoff (~1e-6 at 128 nodes).
+// Outputs, all [N][M] (element (i, j) at j*M + i): Gt = G (FP64); St = S / (N g_scale),
+// Gf = G, wl = 1/D, tau = word-line voltage ratios of the first pass (tau_0 = g_s / D_0,
+// tau_j = tau_{j-1} g_w / D_j), bl = 1/E, xg = g_o z G with z = (K_j + diag G_j)^-1 e_{M-1} (FP32).
 constexpr int kU = 8;
-__global__ void wl_pass_kernel(const double* __restrict__ Gt, const double* __restrict__ wl, double* __restrict__ F,
-                               int K, int k0, int M, int N, double gs, double gw, int first) {
-  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (t >= (long)K * M) return;
-  const int kk = (int)(t / M), i = (int)(t - (long)kk * M);
-  double* f = F + (long)kk * N * M + i;  // node (i, j) at f[j*M]
-  const bool src = (i == k0 + kk);
-  if (first && !src) {
-    for (int j = 0; j < N; ++j) f[(long)j * M] = 0.0;
-    return;
+
+__device__ __forceinline__ void rescale(float& a, float& b) {
+  int e;
+  frexpf(b, &e);
+  a = ldexpf(a, -e);
+  b = ldexpf(b, -e);
+}
+
+// Copy n values with kStage loads in flight per thread: dst[di(t)] = src(t), t < n.
+constexpr int kStage = 16;
+template <typename T, typename S, typename D>
+__device__ __forceinline__ void stage_block(T* dst, int n, S src, D di) {
+  for (int t0 = threadIdx.x; t0 < n; t0 += kStage * blockDim.x) {
+    T v[kStage];
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int t = t0 + u * blockDim.x;
+      v[u] = t < n ? src(t) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < n) dst[di(t)] = v[u];
+    }
   }
-  double tn = 0.0;
-  int j = N - 1;
-  for (; j >= kU - 1; j -= kU) {  // back pass: t_j = (r_j + g_w t_{j+1}) / D_j
-    double r[kU], d[kU];
+}
+
+// One thread per word line, blockDim.x (<= 32) lines per block; their conductances and pivots in
+// shared memory (pitch N + 1).  Dynamic shared memory: blockDim.x (N + 1) (8 + 4) bytes.
+__global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sGj, int M, int N, float gs, float gw,
+                                 double s_scale, double* __restrict__ Gt, float* __restrict__ St,
+                                 float* __restrict__ Gf, float* __restrict__ wl, float* __restrict__ tau) {
+  extern __shared__ double gsm[];
+  const int i0 = blockIdx.x * blockDim.x, rows = min((int)blockDim.x, M - i0), P = N + 1;
+  float* rsm = reinterpret_cast<float*>(gsm + blockDim.x * P);
+  if (sGj == 1)  // consecutive threads along a row
+    stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t / N) * sGi + t % N]; },
+                [&](int t) { return (t / N) * P + t % N; });
+  else           // consecutive threads down a column
+    stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t % rows) * sGi + (long)(t / rows) * sGj]; },
+                [&](int t) { return (t % rows) * P + t / rows; });
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r >= rows) return;
+  const int i = i0 + r;
+  const double* g = gsm + r * P;
+  float* rd = rsm + r * P;
+  double acc = 0.0;
+  float a = 0.0f, b = 1.0f;  // delta = a / b
+  for (int j0 = N - 1; j0 >= 0; j0 -= kU) {
+    const int n = min(kU, j0 + 1);
+    float bj[kU], dj[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      const long o = (long)(j - u) * M;
-      r[u] = first ? 0.0 : Gt[o + i] * f[o];
-      d[u] = wl[o + i];
+      if (u < n) {
+        const float gv = (float)g[j0 - u];
+        const float num = ((j0 - u) == 0 ? gs : gw) * b + gv * b + gw * a;  // D_j b_j
+        bj[u] = b;
+        dj[u] = num;
+        a = gv * b + gw * a;
+        b = num;
+      }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      if (src && j - u == 0) r[u] += gs;
-      tn = (r[u] + gw * tn) * d[u];
-      f[(long)(j - u) * M] = tn;
+      if (u < n) {
+        const int j = j0 - u;
+        const long o = (long)j * M + i;
+        const double gd = g[j];
+        const float w = bj[u] / dj[u];
+        Gt[o] = gd;
+        Gf[o] = (float)gd;
+        acc += gd;
+        St[o] = (float)(acc * s_scale);
+        wl[o] = w;
+        rd[j] = w;
+      }
+    }
+    rescale(a, b);
+  }
+  float t = gs * rd[0];  // forward: the first pass, driven at column 0
+  tau[i] = t;
+  for (int j = 1; j < N; ++j) {
+    t *= gw * rd[j];
+    tau[(long)j * M + i] = t;
+  }
+}
+
+// One thread per bit line, blockDim.x (<= 32) lines per block; their conductances and pivots in
+// shared memory (pitch M + 1).  Dynamic shared memory: 2 blockDim.x (M + 1) floats.
+__global__ void prep_cols_kernel(const float* __restrict__ Gf, int M, int N, float gb, float go,
+                                 float* __restrict__ bl, float* __restrict__ xg) {
+  extern __shared__ float csm[];
+  const int j0 = blockIdx.x * blockDim.x, cols = min((int)blockDim.x, N - j0), P = M + 1;
+  float* gsm = csm;                   // G, then g_o z G
+  float* esm = csm + blockDim.x * P;  // 1/E
+  stage_block(gsm, cols * M, [&](int t) { return Gf[(long)j0 * M + t]; },
+              [&](int t) { return (t / M) * P + t % M; });
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < cols) {
+    float* g = gsm + c * P;
+    float* e = esm + c * P;
+    float a = 0.0f, cc = 1.0f;  // eps = a / cc
+    for (int i0 = 0; i0 < M; i0 += kU) {
+      const int n = min(kU, M - i0);
+      float ci[kU], ei[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (u < n) {
+          const float an = g[i0 + u] * cc + gb * a;
+          const float num = an + ((i0 + u) < M - 1 ? gb : go) * cc;  // E_i c_{i-1}
+          ci[u] = cc;
+          ei[u] = num;
+          a = an;
+          cc = num;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (u < n) e[i0 + u] = ci[u] / ei[u];
+      rescale(a, cc);
+    }
+    float x = e[M - 1];  // unit current at the bottom node: s_i = 0 above it
+    for (int i = M - 1; i >= 0; --i) {
+      g[i] = go * x * g[i];  // G is not read again
+      if (i > 0) x *= gb * e[i - 1];
     }
   }
-  for (; j >= 0; --j) {
-    const long o = (long)j * M;
-    double r = first ? 0.0 : Gt[o + i] * f[o];
+  __syncthreads();
+  for (int t = threadIdx.x; t < cols * M; t += blockDim.x) {  // coalesced: bl, xg are [N][M]
+    const int c2 = t / M, i = t - c2 * M;
+    bl[(long)(j0 + c2) * M + i] = esm[c2 * P + i];
+    xg[(long)(j0 + c2) * M + i] = gsm[c2 * P + i];
+  }
+}
+
+// Chain solves on an [N][pitch] field f (node (i, j) at f[j*pitch + i]).
+// Word line i: w = (L_i + diag G_i)^-1 (G_i o u + g_s [i == k] e_0), written over u (= f).
+__device__ __forceinline__ void wl_solve(float* f, const float* g, const float* d, int pitch, int i, int N, bool src,
+                                         float gs, float gw) {
+  float tn = 0.0f;
+#pragma unroll 4
+  for (int j = N - 1; j >= 0; --j) {  // t_j = (r_j + g_w t_{j+1}) / D_j
+    const int o = j * pitch + i;
+    float r = g[o] * f[o];
     if (src && j == 0) r += gs;
-    tn = (r + gw * tn) * wl[o + i];
+    tn = (r + gw * tn) * d[o];
     f[o] = tn;
   }
-  double w = f[0];  // forward: w_j = (g_w / D_j) w_{j-1} + t_j
-  j = 1;
-  for (; j + kU <= N; j += kU) {
-    double tv[kU], d[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const long o = (long)(j + u) * M;
-      tv[u] = f[o];
-      d[u] = wl[o + i];
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      w = gw * d[u] * w + tv[u];
-      f[(long)(j + u) * M] = w;
-    }
-  }
-  for (; j < N; ++j) {
-    const long o = (long)j * M;
-    w = gw * wl[o + i] * w + f[o];
+  float w = f[i];
+#pragma unroll 4
+  for (int j = 1; j < N; ++j) {  // w_j = (g_w / D_j) w_{j-1} + t_j
+    const int o = j * pitch + i;
+    w = gw * d[o] * w + f[o];
     f[o] = w;
   }
 }
-
-// Bit-line pass, one thread per (kk, j): u_j = (K_j + diag G_j)^-1 (G_j o w_j), written over w.
-__global__ void bl_pass_kernel(const double* __restrict__ Gt, const double* __restrict__ bl, double* __restrict__ F,
-                               int K, int M, int N, double gb) {
-  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (t >= (long)K * N) return;
-  const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
-  double* f = F + ((long)kk * N + j) * M;
-  const double* g = Gt + (long)j * M;
-  const double* e = bl + (long)j * M;
-  double sp = 0.0;
-  int i = 0;
-  for (; i + kU <= M; i += kU) {  // forward: s_i = (r_i + g_b s_{i-1}) / E_i
-    double r[kU], d[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      r[u] = g[i + u] * f[i + u];
-      d[u] = e[i + u];
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      sp = (r[u] + gb * sp) * d[u];
-      f[i + u] = sp;
-    }
+// Bit line j: u = (K_j + diag G_j)^-1 (G_j o w), written over w (= f).
+__device__ __forceinline__ void bl_solve(float* f, const float* g, const float* e, int pitch, int j, int M, float gb) {
+  float* fj = f + j * pitch;
+  const float* gj = g + j * pitch;
+  const float* ej = e + j * pitch;
+  float sp = 0.0f;
+#pragma unroll 4
+  for (int i = 0; i < M; ++i) {  // s_i = (r_i + g_b s_{i-1}) / E_i
+    sp = (gj[i] * fj[i] + gb * sp) * ej[i];
+    fj[i] = sp;
   }
-  for (; i < M; ++i) {
-    sp = (g[i] * f[i] + gb * sp) * e[i];
-    f[i] = sp;
-  }
-  double x = f[M - 1];  // back: x_i = (g_b / E_i) x_{i+1} + s_i
-  i = M - 2;
-  for (; i >= kU - 1; i -= kU) {
-    double sv[kU], d[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      sv[u] = f[i - u];
-      d[u] = e[i - u];
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      x = gb * d[u] * x + sv[u];
-      f[i - u] = x;
-    }
-  }
-  for (; i >= 0; --i) {
-    x = gb * e[i] * x + f[i];
-    f[i] = x;
+  float x = fj[M - 1];
+#pragma unroll 4
+  for (int i = M - 2; i >= 0; --i) {  // x_i = (g_b / E_i) x_{i+1} + s_i
+    x = gb * ej[i] * x + fj[i];
+    fj[i] = x;
   }
 }
 
+// The whole line model of one unit input k in one block.  Shared memory holds the response field,
+// G, and one per-map factor array at a time (bit-line pivots, word-line pivots, sense weights),
+// all [N][M+1]: the odd pitch keeps both the row walks and the column walks free of bank
+// conflicts, and every chain step is a shared-memory access.  Pass 0 is tau in row k.
+__global__ void line_smem_kernel(const float* __restrict__ Gf, const float* __restrict__ wl,
+                                 const float* __restrict__ bl, const float* __restrict__ xg,
+                                 const float* __restrict__ tau, int M, int N, int passes, float gs, float gw, float gb,
+                                 double* __restrict__ T) {
+  extern __shared__ float smem[];
+  const int k = blockIdx.x, P = M + 1;
+  float* Fs = smem;
+  float* Gs = Fs + N * P;
+  float* As = Gs + N * P;
+  auto stage = [&](float* dst, const float* src) {
+    stage_block(dst, M * N, [&](int t) { return src[t]; }, [&](int t) { return (t / M) * P + t % M; });
+  };
+  stage(Gs, Gf);
+  stage_block(Fs, M * N, [&](int t) { return t % M == k ? tau[t] : 0.0f; },
+              [&](int t) { return (t / M) * P + t % M; });
+  for (int p = 1; p < passes; ++p) {
+    stage(As, bl);
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) bl_solve(Fs, Gs, As, P, j, M, gb);
+    __syncthreads();
+    stage(As, wl);
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += blockDim.x) wl_solve(Fs, Gs, As, P, i, N, i == k, gs, gw);
+    __syncthreads();
+  }
+  stage(As, xg);
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float acc = 0.0f;
+#pragma unroll 8
+    for (int i = 0; i < M; ++i) acc = fmaf(As[j * P + i], Fs[j * P + i], acc);
+    T[(long)j * M + k] = acc;
+  }
+}
+
+// The same with the field in global memory (maps whose working set does not fit in shared
+// memory): F[(kk*N + j)*M + i] is node (i, j) for input k = k0 + kk; pass 0 writes tau in row k.
+__global__ void wl_first_kernel(const float* __restrict__ tau, float* __restrict__ F, int K, int k0, int M, int N) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)K * M * N) return;
+  const int kk = (int)(t / ((long)M * N));
+  const long o = t - (long)kk * M * N;
+  const int i = (int)(o % M);
+  F[t] = i == k0 + kk ? tau[o] : 0.0f;
+}
+__global__ void wl_pass_kernel(const float* __restrict__ Gf, const float* __restrict__ wl, float* __restrict__ F,
+                               int K, int k0, int M, int N, float gs, float gw) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)K * M) return;
+  const int kk = (int)(t / M), i = (int)(t - (long)kk * M);
+  wl_solve(F + (long)kk * N * M, Gf, wl, M, i, N, i == k0 + kk, gs, gw);
+}
+__global__ void bl_pass_kernel(const float* __restrict__ Gf, const float* __restrict__ bl, float* __restrict__ F,
+                               int K, int M, int N, float gb) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)K * N) return;
+  const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
+  bl_solve(F + (long)kk * N * M, Gf, bl, M, j, M, gb);
+}
 // Sense currents of the last word-line pass: T[j*M + k] = sum_i xg(i, j) w(i, j; k).
-__global__ void line_transfer_kernel(const double* __restrict__ xg, const double* __restrict__ F, int K, int k0, int M,
+__global__ void line_transfer_kernel(const float* __restrict__ xg, const float* __restrict__ F, int K, int k0, int M,
                                      int N, double* __restrict__ T) {
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= (long)K * N) return;
   const int kk = (int)(t / N), j = (int)(t - (long)kk * N);
-  const double* f = F + ((long)kk * N + j) * M;
-  const double* z = xg + (long)j * M;
-  double acc[kU] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int i = 0;
-  for (; i + kU <= M; i += kU) {
-#pragma unroll
-    for (int u = 0; u < kU; ++u) acc[u] += z[i + u] * f[i + u];
-  }
-  for (; i < M; ++i) acc[0] += z[i] * f[i];
-  double a = 0.0;
-#pragma unroll
-  for (int u = 0; u < kU; ++u) a += acc[u];
-  T[(long)j * M + k0 + kk] = a;
+  const float* f = F + ((long)kk * N + j) * M;
+  const float* z = xg + (long)j * M;
+  float acc = 0.0f;
+#pragma unroll 8
+  for (int i = 0; i < M; ++i) acc = fmaf(z[i], f[i], acc);
+  T[(long)j * M + k0 + kk] = acc;
 }
 
 // ---- inference inputs: the first layer splits into a per-column and a per-vector product ------
@@ -277,21 +375,37 @@ __global__ void infer_gt32_kernel(const double* Gt, const double* Tl, int M, int
 }
 
 // I_ideal[b][j] = V_b . G(:, j), I_line[b][j] = V_b . T_line(:, j), FP32 accumulation (their
-// relative error, ~1e-7, is far below the network's); one block per input vector b
-__global__ void infer_currents_kernel(const double* V, const float* G32, const float* T32, int M, int N,
+// relative error, ~1e-7, is far below the network's); one block per kVB input vectors, so each
+// load of G and T_line serves kVB vectors
+constexpr int kVB = 8;
+__global__ void infer_currents_kernel(const double* V, const float* G32, const float* T32, int M, int N, int B,
                                       double* Iid, double* Iln) {
-  extern __shared__ float vs[];
-  const int b = blockIdx.x;
-  for (int i = threadIdx.x; i < M; i += blockDim.x) vs[i] = (float)V[(long)b * M + i];
+  extern __shared__ float vs[];  // [kVB][M]
+  const int b0 = blockIdx.x * kVB;
+  for (int t = threadIdx.x; t < kVB * M; t += blockDim.x) {
+    const int u = t / M, i = t - u * M;
+    vs[t] = b0 + u < B ? (float)V[(long)(b0 + u) * M + i] : 0.0f;
+  }
   __syncthreads();
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    float a = 0.0f, c = 0.0f;
+    float a[kVB], c[kVB];
+#pragma unroll
+    for (int u = 0; u < kVB; ++u) a[u] = c[u] = 0.0f;
+#pragma unroll 4
     for (int i = 0; i < M; ++i) {
-      a = fmaf(vs[i], G32[(long)i * N + j], a);
-      c = fmaf(vs[i], T32[(long)i * N + j], c);
+      const float g = G32[(long)i * N + j], t = T32[(long)i * N + j];
+#pragma unroll
+      for (int u = 0; u < kVB; ++u) {
+        a[u] = fmaf(vs[u * M + i], g, a[u]);
+        c[u] = fmaf(vs[u * M + i], t, c[u]);
+      }
     }
-    Iid[(long)b * N + j] = a;
-    Iln[(long)b * N + j] = c;
+#pragma unroll
+    for (int u = 0; u < kVB; ++u)
+      if (b0 + u < B) {
+        Iid[(long)(b0 + u) * N + j] = a[u];
+        Iln[(long)(b0 + u) * N + j] = c[u];
+      }
   }
 }
 
@@ -449,9 +563,9 @@ __global__ void finalize_kernel(const float* out, const float* b3, const double*
   const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const double ii = Iid[r];
-  const double n0 = (double)(out[2 * r] + b3[0]), n1 = (double)(out[2 * r + 1] + b3[1]);
-  const double Ir = Iln[r] + ii * (mu + sigma * n0);
-  const double e = cal * sigma * exp(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
+  const float n0 = out[2 * r] + b3[0], n1 = out[2 * r + 1] + b3[1];
+  const double Ir = Iln[r] + ii * (mu + sigma * (double)n0);
+  const double e = cal * sigma * (double)expf(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
   I[r] = Ir;
   if (est) est[r] = e;
   if (flag && !(e <= bound)) flag[r / N] = 1;
@@ -503,7 +617,7 @@ struct xbar_surrogate_s {
   Buf X, H1, H2, dZ2, dZ1, y, out, Iid, Iln, flag, idx, gV, gI;
   // per-map line model and feature columns: [N][M]
   int passes = 1;
-  Buf Gt, St, Tl, wl, bl, xg, field;
+  Buf Gt, Gf, tau, St, Tl, wl, bl, xg, field;
   // inference: split first layer and FP32 copies for the current contractions
   Buf xgs, xv, Pm, Qm, g32, t32;
   // training set
@@ -733,29 +847,53 @@ extern "C" xbar_status xbar_surrogate_grad(xbar_surrogate_t s, int R, const floa
 static xbar_status map_prep(xbar_surrogate_t s, const double* G, long sGi, long sGj) {
   const int M = s->M, N = s->N;
   const size_t mn = (size_t)M * N;
-  // inputs per chunk of the response field: at most 256 MiB of it
-  const int K = (int)std::max<size_t>(1, std::min<size_t>((size_t)M, ((size_t)256 << 20) / (mn * 8)));
   XB_CUDA(ensure(s->A, s->Gt, mn * 8));
+  XB_CUDA(ensure(s->A, s->Gf, mn * 4));
+  XB_CUDA(ensure(s->A, s->tau, mn * 4));
   XB_CUDA(ensure(s->A, s->St, mn * 4));
   XB_CUDA(ensure(s->A, s->Tl, mn * 8));
-  XB_CUDA(ensure(s->A, s->wl, mn * 8));
-  XB_CUDA(ensure(s->A, s->bl, mn * 8));
-  XB_CUDA(ensure(s->A, s->xg, mn * 8));
-  XB_CUDA(ensure(s->A, s->field, (size_t)K * mn * 8));
-  const double gs = 1.0 / s->R[0], gw = 1.0 / s->R[1], gb = 1.0 / s->R[2], go = 1.0 / s->R[3];
-  double* Gt = (double*)s->Gt.p;
-  double* F = (double*)s->field.p;
-  prep_rows_kernel<<<(M + 127) / 128, 128, 0, s->st>>>(G, sGi, sGj, M, N, gs, gw, 1.0 / (N * s->gs), Gt,
-                                                       (float*)s->St.p, (double*)s->wl.p);
-  prep_cols_kernel<<<(N + 127) / 128, 128, 0, s->st>>>(Gt, M, N, gb, go, (double*)s->bl.p, (double*)s->xg.p);
-  for (int k0 = 0; k0 < M; k0 += K) {
-    const int Kc = std::min(K, M - k0);
-    const unsigned gm = (unsigned)(((long)Kc * M + 127) / 128), gn = (unsigned)(((long)Kc * N + 127) / 128);
-    for (int p = 0; p < s->passes; ++p) {
-      wl_pass_kernel<<<gm, 128, 0, s->st>>>(Gt, (const double*)s->wl.p, F, Kc, k0, M, N, gs, gw, p == 0);
-      if (p + 1 < s->passes) bl_pass_kernel<<<gn, 128, 0, s->st>>>(Gt, (const double*)s->bl.p, F, Kc, M, N, gb);
+  XB_CUDA(ensure(s->A, s->wl, mn * 4));
+  XB_CUDA(ensure(s->A, s->bl, mn * 4));
+  XB_CUDA(ensure(s->A, s->xg, mn * 4));
+  const float gs = (float)(1.0 / s->R[0]), gw = (float)(1.0 / s->R[1]), gb = (float)(1.0 / s->R[2]),
+              go = (float)(1.0 / s->R[3]);
+  const float* Gf = (const float*)s->Gf.p;
+  const float* wl = (const float*)s->wl.p;
+  const float* bl = (const float*)s->bl.p;
+  const float* xg = (const float*)s->xg.p;
+  const float* tau = (const float*)s->tau.p;
+  // one warp per SM: the chains are sequential, and several warps of them on one SM would only
+  // share its pipes
+  // lines per block: up to a warp, as many as the shared-memory budget holds (at least one)
+  const int rb = (int)std::max<size_t>(1, std::min<size_t>(32, kPrepSmemMax / ((size_t)(N + 1) * 12)));
+  const int cb = (int)std::max<size_t>(1, std::min<size_t>(32, kPrepSmemMax / ((size_t)(M + 1) * 8)));
+  const size_t smr = (size_t)rb * (N + 1) * 12, smc = (size_t)cb * (M + 1) * 8;
+  if (smr > kPrepSmemMax || smc > kPrepSmemMax) return set_error(XBAR_EINVAL, "map too large for the line model");
+  XB_CUDA(cudaFuncSetAttribute(prep_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  XB_CUDA(cudaFuncSetAttribute(prep_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+  prep_rows_kernel<<<(M + rb - 1) / rb, rb, smr, s->st>>>(G, sGi, sGj, M, N, gs, gw, 1.0 / (N * s->gs), (double*)s->Gt.p,
+                                                    (float*)s->St.p, (float*)s->Gf.p, (float*)s->wl.p,
+                                                    (float*)s->tau.p);
+  prep_cols_kernel<<<(N + cb - 1) / cb, cb, smc, s->st>>>(Gf, M, N, gb, go, (float*)s->bl.p, (float*)s->xg.p);
+  const size_t smem = 3 * (size_t)N * (M + 1) * 4;
+  if (smem <= kLineSmemMax) {  // one block per unit input, everything in shared memory
+    const int threads = std::min(1024, round_up(std::max(M, N), 32));
+    XB_CUDA(cudaFuncSetAttribute(line_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    line_smem_kernel<<<M, threads, smem, s->st>>>(Gf, wl, bl, xg, tau, M, N, s->passes, gs, gw, gb, (double*)s->Tl.p);
+  } else {  // the field in global memory, in chunks of inputs of at most 256 MiB
+    const int K = (int)std::max<size_t>(1, std::min<size_t>((size_t)M, ((size_t)256 << 20) / (mn * 4)));
+    XB_CUDA(ensure(s->A, s->field, (size_t)K * mn * 4));
+    float* F = (float*)s->field.p;
+    for (int k0 = 0; k0 < M; k0 += K) {
+      const int Kc = std::min(K, M - k0);
+      const unsigned gm = (unsigned)(((long)Kc * M + 127) / 128), gn = (unsigned)(((long)Kc * N + 127) / 128);
+      wl_first_kernel<<<(unsigned)(((long)Kc * mn + 255) / 256), 256, 0, s->st>>>(tau, F, Kc, k0, M, N);
+      for (int p = 1; p < s->passes; ++p) {
+        bl_pass_kernel<<<gn, 128, 0, s->st>>>(Gf, bl, F, Kc, M, N, gb);
+        wl_pass_kernel<<<gm, 128, 0, s->st>>>(Gf, wl, F, Kc, k0, M, N, gs, gw);
+      }
+      line_transfer_kernel<<<gn, 128, 0, s->st>>>(xg, F, Kc, k0, M, N, (double*)s->Tl.p);
     }
-    line_transfer_kernel<<<gn, 128, 0, s->st>>>((const double*)s->xg.p, F, Kc, k0, M, N, (double*)s->Tl.p);
   }
   XB_CUDA(cudaGetLastError());
   return XBAR_OK;
@@ -910,8 +1048,8 @@ static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, lo
                                                                            (__nv_bfloat16*)s->xv.p);
   infer_gt32_kernel<<<(unsigned)(((long)M * N + 255) / 256), 256, 0, s->st>>>(
       (const double*)s->Gt.p, (const double*)s->Tl.p, M, N, (float*)s->g32.p, (float*)s->t32.p);
-  infer_currents_kernel<<<B, 128, M * sizeof(float), s->st>>>(V, (const float*)s->g32.p, (const float*)s->t32.p, M, N,
-                                                              (double*)s->Iid.p, (double*)s->Iln.p);
+  infer_currents_kernel<<<(B + kVB - 1) / kVB, 128, kVB * M * sizeof(float), s->st>>>(
+      V, (const float*)s->g32.p, (const float*)s->t32.p, M, N, B, (double*)s->Iid.p, (double*)s->Iln.p);
   XB_CUDA(cudaGetLastError());
   GemmBf16Params g;
   memset(&g, 0, sizeof(g));
@@ -923,7 +1061,7 @@ static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, lo
   g.B = s->W1b;
   g.sBn = Fp;
   g.sBk = 1;
-  g.mode = GEMM_EPI_STORE;
+  g.mode = GEMM_EPI_STORE;  // not split over K: prediction stays deterministic
   g.ldc = kH;
   g.M = (int)Npad;
   g.A = (const __nv_bfloat16*)s->xgs.p;

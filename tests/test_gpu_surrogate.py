@@ -46,16 +46,20 @@ def test_params_roundtrip():
 
 
 @pytest.mark.parametrize("M,N,B,P", [(40, 24, 7, 1), (40, 24, 7, 2), (33, 50, 3, 3), (128, 128, 3, 2),
-                                     (7, 5, 3, 4), (1, 1, 2, 2), (1, 9, 2, 2), (9, 1, 2, 3)])
+                                     (7, 5, 3, 4), (1, 1, 2, 2), (1, 9, 2, 2), (9, 1, 2, 3),
+                                     (160, 160, 2, 2), (200, 90, 2, 3)])
 def test_line_model_matches_oracle(M, N, B, P):
-    """All-zero network parameters and mu = 0 leave the line model: I = I_line exactly."""
+    """All-zero network parameters and mu = 0 leave the line model: I = I_line exactly.
+    160 x 160 and 200 x 90 exceed the shared-memory form and run the global-memory kernels."""
     G, V = inputs.crossbar(M, N, B, seed=7 * M + N)
     s = xbar.Surrogate(M, N, CIRCUIT, passes=P)
     s.set_params(np.zeros(MLP.n_params(M), dtype=np.float32))
     I = np.zeros((B, N))
     s.predict(G, V, I)
-    # T_line is FP64; the contraction with V accumulates in FP32 (relative error ~1e-7)
-    np.testing.assert_allclose(I, MLP.line_currents(G, V, CIRCUIT, P), rtol=5e-6, atol=0)
+    # the line model's chains run in FP32 over sums of positive terms: relative error below
+    # (chain length) x (a few roundings) x 2^-24, i.e. < 3e-5 up to 128 nodes per line
+    err = np.max(np.abs(I / MLP.line_currents(G, V, CIRCUIT, P) - 1))
+    assert err <= 3e-5, err
     s.destroy()
 
 
