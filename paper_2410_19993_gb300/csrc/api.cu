@@ -139,6 +139,10 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   XB_ALLOC(m.hs32, nv * 4);
   XB_ALLOC(m.src32, (size_t)m.Mp * 4);
   XB_ALLOC(m.Coff, nv * m.Mp * 8);
+  XB_ALLOC(m.Gc2, nv * 8);
+  XB_ALLOC(m.h2, nv * 8);
+  XB_ALLOC(m.tha2, nv * 8);
+  XB_ALLOC(m.thc2, nv * 8);
   XB_ALLOC(h->status, sizeof(unsigned));
   double* Gd = nullptr;
   XB_ALLOC(Gd, (size_t)M * N * 8);
@@ -378,8 +382,14 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     XB_CUDA(ensure(h->A, h->maxrel, 16));
     XB_CUDA(ensure(h->A, h->rmax, 16));
     rp.w = (double*)h->w64.p;
+    rp.w2 = (float2*)h->w64.p;
     rp.dhat = (const float*)h->dhat.p;
     rp.phi = (double*)h->phi.p;
+    rp.phi2 = (float2*)h->phi.p;
+    rp.Gc2 = m.Gc2;
+    rp.h2 = m.h2;
+    rp.tha2 = m.tha2;
+    rp.thc2 = m.thc2;
     rp.rhat = (float*)h->rhat.p;
     rp.rmax = (unsigned long long*)h->rmax.p;
     SweepParams<float> sp;
@@ -457,6 +467,10 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       PhaseScope ps(h, XBAR_PHASE_UPDATE);
       XB_CUDA(launch_update(rp, 0, st));
     }
+    if (want_v) {  // the node-voltage output reads the state as doubles
+      PhaseScope ps(h, XBAR_PHASE_OUTPUT);
+      XB_CUDA(launch_pair_to_double(rp, st));
+    }
   }
   if (want_v) {
     PhaseScope ps(h, XBAR_PHASE_OUTPUT, 1 + (dvWL ? 1 : 0) + (dvBL ? 1 : 0));
@@ -527,6 +541,8 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   rp.gs = m.gs; rp.gw = m.gw; rp.Gc = m.Gc; rp.dW = m.dW; rp.h = m.h; rp.tha = m.tha; rp.thc = m.thc;
   rp.s32 = m.s32; rp.V = dV; rp.I = dI; rp.status = h->status;
   rp.w = (double*)h->w64.p; rp.dhat = (const float*)h->dhat.p; rp.phi = (double*)h->phi.p;
+  rp.w2 = (float2*)h->w64.p; rp.phi2 = (float2*)h->phi.p;
+  rp.Gc2 = m.Gc2; rp.h2 = m.h2; rp.tha2 = m.tha2; rp.thc2 = m.thc2;
   rp.rhat = (float*)h->rhat.p; rp.rmax = &state->rmax;
   SweepParams<float> sp;
   sp.M = M; sp.Mp = Mp; sp.N = N; sp.B = B; sp.Bp = Bp; sp.Bpad = Bpad;

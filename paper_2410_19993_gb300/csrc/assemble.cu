@@ -105,6 +105,14 @@ __global__ void asm_scale_kernel(MapDev m) {
   m.s32[o] = (float)s;
   m.e32[o] = (float)e_eq;
   m.hs32[o] = (float)(s * m.h[o]);
+  auto pair = [](double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+  };
+  m.Gc2[o] = pair(m.Gc[o]);
+  m.h2[o] = pair(m.h[o]);
+  m.tha2[o] = pair(m.tha[o]);
+  m.thc2[o] = pair(m.thc[o]);
   if (j == 0) {
     m.src_eq[i] = real ? m.gs * s : 0.0;
     m.src_pl[i] = real ? m.gs : 0.0;

@@ -34,6 +34,12 @@ struct MapDev {
   float* e32 = nullptr;
   float* hs32 = nullptr;
   float* src32 = nullptr;
+  // float pairs (hi + lo, ~48 significant bits) of the coefficients the refinement's residual and
+  // update use: the FP64 arithmetic of the mixed path runs on the FP32 pipe
+  float2* Gc2 = nullptr;
+  float2* h2 = nullptr;
+  float2* tha2 = nullptr;
+  float2* thc2 = nullptr;
 };
 
 // ---- assembly ---------------------------------------------------------------------------------
@@ -156,9 +162,18 @@ struct ResidParams {
   unsigned long long* rmax;  // bit pattern of max |r| (non-negative double)
   unsigned* status;
   const int* skip;           // if set and nonzero at launch, the kernel does nothing
+  // mixed path: the state w and the scratch phi as float pairs (in the w / phi buffers)
+  float2* w2;
+  float2* phi2;
+  const float2* Gc2;
+  const float2* h2;
+  const float2* tha2;
+  const float2* thc2;
 };
-// w = (first ? 0 : w) + s * dhat ; I = h . w
+// w = (first ? 0 : w) + s * dhat ; I = h . w    (float-pair state w2)
 cudaError_t launch_update(const ResidParams& p, int first, cudaStream_t st);
+// w2 (float pairs) -> w (double), in place: the node-voltage output reads doubles
+cudaError_t launch_pair_to_double(const ResidParams& p, cudaStream_t st);
 // rhat = s * (b - K w)   with K the word-line system after bit-line elimination
 cudaError_t launch_resid(const ResidParams& p, cudaStream_t st);
 // bit-line voltages u = T^-1 (G o w) into `u` ([N][Mp][Bpad]), in place of phi

@@ -1,18 +1,25 @@
-// resid.cu -- FP64 steps of mixed-precision iterative refinement, and node-voltage output.
+// resid.cu -- extended-precision steps of mixed-precision iterative refinement, and node-voltage
+// output.
 //
-// The refinement state is the FP64 vector w of word-line node voltages.  Bit-line voltages are
-// not stored: for any w they follow from the bit-line rows of the nodal system (Eqs. 3, 4, 7),
+// The refinement state is the vector w of word-line node voltages, held as float pairs
+// (hi + lo, ~48 significant bits).  Bit-line voltages are not stored: for any w they follow from
+// the bit-line rows of the nodal system (Eqs. 3, 4, 7),
 //     T_j u_j = G_j o w_j     (tridiagonal chain of bit line j),
-// solved here in FP64 with the same subtraction-free pivots as the assembly.  The word-line rows
-// (Eqs. 1, 2, 5, 6) then give the residual of the nodal system restricted to word-line nodes:
+// solved with the same subtraction-free pivots as the assembly.  The word-line rows (Eqs. 1, 2,
+// 5, 6) then give the residual of the nodal system restricted to word-line nodes,
 //     r(i,j) = b(i,j) + g_w (w(i,j-1) + w(i,j+1)) + G_ij u(i,j) - dW(i,j) w(i,j),
-// b = g_s V_i at j = 0.  The bit-line rows hold exactly by construction of u, so r is the full
-// residual of the 2MN system.  These two kernels and the update w += s o dhat are the only FP64
-// arithmetic of the mixed path.
+// b = g_s V_i at j = 0, evaluated as a sum of branch currents.  The bit-line rows hold exactly by
+// construction of u, so r is the full residual of the 2MN system.  The residual and the update
+// w += s o dhat are the only extended-precision arithmetic of the mixed path; they run in float
+// pairs on the FP32 pipe (FP64 is 1/64 of its rate on this part).  Their error, ~2^-48 of each
+// branch current, bounds what refinement can reach: about 1e-10 relative current error at
+// 256 x 256, against the 1e-8 target.
 //
 // One thread per (column j, input vector b); consecutive threads take consecutive b, so every
 // access to the [N][Mp][Bpad] arrays is coalesced.  Loops run along the chain i.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "handle.h"
@@ -20,58 +27,97 @@
 
 namespace xbar {
 
-// w = (first ? 0 : w) + s * dhat  (FP64),  I[b][j] = h_j . w_j  (FP64)
+// ---- float-pair arithmetic ----------------------------------------------------------------------
+// A value is hi + lo with |lo| <= ulp(hi) / 2 (~48 significant bits).  Sums use the error-free
+// two-sum transformation of the leading parts plus the sum of the trailing parts; products use
+// the FMA residual of the leading product (Dekker / Knuth transformations, as in double-double
+// arithmetic).  Only the FP32 pipe is used: on this part it runs 64 times the FP64 rate.
+struct fp2 {
+  float hi, lo;
+};
+__device__ __forceinline__ fp2 quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ fp2 two_sum(float a, float b) {
+  const float s = a + b, v = s - a;
+  return {s, (a - (s - v)) + (b - v)};
+}
+__device__ __forceinline__ fp2 padd(fp2 x, fp2 y) {
+  const fp2 t = two_sum(x.hi, y.hi);
+  return quick_two_sum(t.hi, t.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ fp2 psub(fp2 x, fp2 y) { return padd(x, fp2{-y.hi, -y.lo}); }
+__device__ __forceinline__ fp2 pmul(fp2 x, fp2 y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ fp2 ld2(const float2* a, size_t o) {
+  const float2 v = a[o];
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st2(float2* a, size_t o, fp2 v) { a[o] = make_float2(v.hi, v.lo); }
+__device__ __forceinline__ fp2 split(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+
+// w = (first ? 0 : w) + s * dhat,  I[b][j] = h_j . w_j   (float pairs; I written as a double)
 __global__ void update_kernel(ResidParams p, int first) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (b >= p.Bpad || j >= p.N) return;
   const size_t base = (size_t)j * p.Mp;
-  double Iacc = 0.0;
+  fp2 Iacc{0.0f, 0.0f};
   for (int i = 0; i < p.M; ++i) {
     const size_t o = (base + i) * p.Bpad + b;
     const float d = p.s32[base + i] * p.dhat[o];
-    const double wn = (first ? 0.0 : p.w[o]) + (double)d;
-    p.w[o] = wn;
-    Iacc = fma(p.h[base + i], wn, Iacc);
+    const fp2 wn = first ? fp2{d, 0.0f} : padd(ld2(p.w2, o), fp2{d, 0.0f});
+    st2(p.w2, o, wn);
+    Iacc = padd(Iacc, pmul(ld2(p.h2, base + i), wn));
   }
-  if (b < p.B) p.I[(size_t)b * p.N + j] = Iacc;
+  if (b < p.B) p.I[(size_t)b * p.N + j] = (double)Iacc.hi + (double)Iacc.lo;
 }
 
-// forward half of the bit-line chain solve: phi_i = tha_i w_i + thc_i phi_{i-1}
-__device__ __forceinline__ void chain_forward(const ResidParams& p, int j, int b) {
-  const size_t base = (size_t)j * p.Mp;
-  double phi = 0.0;
-  for (int i = 0; i < p.M; ++i) {
-    const size_t o = (base + i) * p.Bpad + b;
-    phi = fma(p.thc[base + i], phi, p.tha[base + i] * p.w[o]);
-    p.phi[o] = phi;
-  }
-}
-
+// Residual of the word-line rows (Eqs. 1, 2, 5, 6) as the sum of the branch currents into node
+// (i, j), each formed from a voltage difference (neighbouring voltages differ by millivolts, so
+// the differences keep full relative accuracy in pairs):
+//   r = [j > 0] g_w (w_{j-1} - w) + [j < N-1] g_w (w_{j+1} - w) + [j = 0] g_s (V_i - w) + G (u - w),
+// identical to b + g_w (w_{j-1} + w_{j+1}) + G u - dW w.  u = T^-1 (G o w) by the bit-line chain
+// (forward phi_i = tha_i w_i + thc_i phi_{i-1}, back u_i = phi_i + thc_i u_{i+1}; all terms >= 0).
 __global__ void resid_kernel(ResidParams p) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (b >= p.Bpad || j >= p.N) return;
-  chain_forward(p, j, b);
   const size_t base = (size_t)j * p.Mp;
+  {
+    fp2 phi{0.0f, 0.0f};
+    for (int i = 0; i < p.M; ++i) {
+      const size_t o = (base + i) * p.Bpad + b;
+      phi = padd(pmul(ld2(p.thc2, base + i), phi), pmul(ld2(p.tha2, base + i), ld2(p.w2, o)));
+      st2(p.phi2, o, phi);
+    }
+  }
   const bool has_l = j > 0, has_r = j + 1 < p.N;
   const bool src = (j == 0) && (b < p.B);
-  double u = 0.0;
+  const fp2 gw = split(p.gw), gs = split(p.gs);
+  fp2 u{0.0f, 0.0f};
   float rmax = 0.0f;  // |r| tracked in FP32: only its magnitude is reported
   const size_t col = (size_t)p.Mp * p.Bpad;
   for (int i = p.M - 1; i >= 0; --i) {
     const size_t o = (base + i) * p.Bpad + b;
-    u = fma(p.thc[base + i], u, p.phi[o]);  // u_i = phi_i + thc_i u_{i+1}
-    const double wi = p.w[o];
-    double nb = has_l ? p.w[o - col] : 0.0;
-    if (has_r) nb = has_l ? nb + p.w[o + col] : p.w[o + col];
-    double r = src ? p.gs * p.V[(size_t)b * p.M + i] : 0.0;
-    r = fma(p.gw, nb, r);
-    r = fma(p.Gc[base + i], u, r);
-    r = fma(-p.dW[base + i], wi, r);
-    const float rf = (float)r;
+    u = padd(ld2(p.phi2, o), pmul(ld2(p.thc2, base + i), u));
+    const fp2 wi = ld2(p.w2, o);
+    fp2 r = pmul(ld2(p.Gc2, base + i), psub(u, wi));
+    if (has_l) r = padd(r, pmul(gw, psub(ld2(p.w2, o - col), wi)));
+    if (has_r) r = padd(r, pmul(gw, psub(ld2(p.w2, o + col), wi)));
+    if (src) r = padd(r, pmul(gs, psub(split(p.V[(size_t)b * p.M + i]), wi)));
+    const float rf = r.hi + r.lo;
     rmax = fmaxf(rmax, fabsf(rf));
     p.rhat[o] = rf * p.s32[base + i];
   }
@@ -82,7 +128,26 @@ __global__ void resid_kernel(ResidParams p) {
     atomicMax(p.rmax, (unsigned long long)__double_as_longlong((double)rmax));
 }
 
-// bit-line voltages u = T^-1 (G o w), written over the scratch array `u`
+// forward half of the bit-line chain solve in FP64 (node-voltage output):
+// phi_i = tha_i w_i + thc_i phi_{i-1}
+__device__ __forceinline__ void chain_forward(const ResidParams& p, int j, int b) {
+  const size_t base = (size_t)j * p.Mp;
+  double phi = 0.0;
+  for (int i = 0; i < p.M; ++i) {
+    const size_t o = (base + i) * p.Bpad + b;
+    phi = fma(p.thc[base + i], phi, p.tha[base + i] * p.w[o]);
+    p.phi[o] = phi;
+  }
+}
+
+// w2 -> w in place (same 8 bytes per entry): each thread converts the entries it reads
+__global__ void pair_to_double_kernel(ResidParams p, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = p.w2[k];
+    p.w[k] = (double)v.x + (double)v.y;
+  }
+}
+
 __global__ void blvolt_kernel(ResidParams p, double* u_out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
@@ -102,6 +167,13 @@ __global__ void blvolt_kernel(ResidParams p, double* u_out) {
 cudaError_t launch_update(const ResidParams& p, int first, cudaStream_t st) {
   dim3 grid((p.Bpad + 127) / 128, p.N);
   update_kernel<<<grid, 128, 0, st>>>(p, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_to_double(const ResidParams& p, cudaStream_t st) {
+  const size_t n = (size_t)p.N * p.Mp * p.Bpad;
+  const int blocks = (int)std::min<size_t>(4096, (n + 255) / 256);
+  pair_to_double_kernel<<<blocks, 256, 0, st>>>(p, n);
   return cudaGetLastError();
 }
 
