@@ -63,7 +63,7 @@ __device__ __forceinline__ void rank16_update(float (&acc)[16], const float* __r
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
     factor_cluster_kernel(const FactorParams<float>* __restrict__ maps, int C, unsigned* status) {
   constexpr int R = kRows;  // rows per block = panel width
   const FactorParams<float> p = maps[blockIdx.x / C];
@@ -167,28 +167,41 @@ __global__ void __launch_bounds__(kThreads)
     for (int pp = 0; pp < C; ++pp) {
       const int P0 = pp * R;
       if ((int)g == pp) {
-        // owner: invert the R x R pivot block (scalar sweep, double-buffered, one reciprocal per pivot)
-        for (int t = tid; t < R * R; t += kThreads) Dm[t] = rows[(size_t)(t / R) * Mp + P0 + t % R];
-        __syncthreads();
-        if (tid == 0) rinv[0] = 1.0f / Dm[0];
-        for (int q = 0; q < R; ++q) {
-          __syncthreads();
-          const float* Dc = Dm + (q & 1) * R * R;
-          float* Dn = Dm + ((q + 1) & 1) * R * R;
-          const float ri = rinv[q];
-          for (int t = tid; t < R * R; t += kThreads) {
-            const int a = t / R, b = t - a * R;
-            float v;
-            if (a == q && b == q) v = ri;
-            else if (a == q) v = Dc[q * R + b] * ri;
-            else if (b == q) v = -Dc[a * R + q] * ri;
-            else v = Dc[t] - Dc[a * R + q] * Dc[q * R + b] * ri;
-            Dn[t] = v;
-            if (q + 1 < R && a == q + 1 && b == q + 1) rinv[q + 1] = 1.0f / v;
+        // owner: invert the R x R pivot block in one warp's registers (Gauss-Jordan, no pivoting:
+        // the block is symmetric positive definite).  Lane l holds column l % 16 of rows
+        // 8 (l / 16) .. 8 (l / 16) + 7; each pivot's row, column and diagonal arrive by shuffles,
+        // so the sweep needs no block-wide barrier.
+        static_assert(R == 16, "register layout assumes 16 x 16 pivot blocks");
+        if (warp == 0) {
+          const int b = lane & 15, a0 = (lane >> 4) * 8;
+          float d[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(a0 + e) * Mp + P0 + b];
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const int qe = q & 7;
+            const float piv = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | q);  // D[q][q]
+            const float ri = 1.0f / piv;
+            const float rowq = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | b);  // D[q][b]
+            float colq[8];  // D[a0 + e][q]
+#pragma unroll
+            for (int e = 0; e < 8; ++e) colq[e] = __shfl_sync(0xffffffffu, d[e], (lane & 16) | q);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int a = a0 + e;
+              float v;
+              if (a == q && b == q) v = ri;
+              else if (a == q) v = rowq * ri;
+              else if (b == q) v = -colq[e] * ri;
+              else v = d[e] - colq[e] * rowq * ri;
+              d[e] = v;
+            }
           }
+#pragma unroll
+          for (int e = 0; e < 8; ++e) Dm[(a0 + e) * R + b] = d[e];
         }
         __syncthreads();
-        const float* Dinv = Dm + (R & 1) * R * R;
+        const float* Dinv = Dm;
         // new panel rows: D x (old panel rows) outside the panel columns, D inside
         for (int k = tid; k < Mp; k += kThreads) {
           float col[R], acc[R];
