@@ -292,8 +292,14 @@ def run_xbar(args):
         bound, peak, note = "alu", peaks["fp32_tflops"], "FP32 FMA pipe, 152 SM x 128 lanes x 2 x max SM clock"
     else:
         bound, peak, note = "alu", peaks["fp64_tflops"], "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock"
+    traffic, traffic_note = None, None
+    if dom == "sweep" and (M, N) == (256, 256) and bound == "tensor":
+        # ncu DRAM read + write of one sweep_tc_kernel launch at B = 2048 (2.351 GB), scaled by
+        # the vectors of this launch: the kernel's streams are per vector
+        traffic = 2.351e9 * B / 2048
+        traffic_note = "ncu dram__bytes_read+write at B=2048 scaled by B (profiles/sweep_tc_xbar256_B2048.md)"
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_note": note,
+                "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note, "peak_note": note,
                 "work_per_launch": work, "ms_per_launch": ms_launch}
 
     cpu = None
@@ -306,9 +312,9 @@ def run_xbar(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refinement", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f32-pair refinement", "data": "synthetic",
         "config": {"workload": args.workload + (f"_B{B}" if args.batch else ""), "M": M, "N": N, "B": B,
-                   "R_s": R[0], "R_w": R[1], "R_b": R[2], "R_sense": R[3], "precision": "fp32 factor+sweeps, fp64 residual/update", "tol": TOL,
+                   "R_s": R[0], "R_w": R[1], "R_b": R[2], "R_sense": R[3], "precision": "fp32 factor+sweeps (split-TF32 tensor cores), float-pair (~48-bit) residual/update", "tol": TOL,
                    "step": "set_conductances + factor + solve (all refinement)",
                    "l2": "working set per step (>6 GB) exceeds the 129 MB L2", "parallelism": f"replicas{world}"},
         "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.fp64_steps,
@@ -431,7 +437,7 @@ def run_tiles(args):
     out = {
         "metric": METRIC, "value": d.sum(total * args.steps) / t_mixed, "unit": UNIT, "n_gpus": d.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refinement",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f32-pair refinement",
         "data": "synthetic",
         "config": {"workload": "fc784_256_10_tiles", "tiles": len(tiles),
                    "shapes": {f"{m}x{n}": sum(t.G.shape == (m, n) for t in tiles)
@@ -567,7 +573,7 @@ def run_surrogate(args):
         "metric": "surrogate solves/s (per-column MLP + exact fallback above 1% estimated error)",
         "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_sur / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 network, fp64 line model", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16 network, fp32 line model", "data": "synthetic",
         "config": {"workload": "surrogate128", "M": M, "N": N, "R_s": R[0], "R_w": R[1], "R_b": R[2],
                    "R_sense": R[3], "train": f"{x['train_maps']} maps x {x['train_B']} vectors",
                    "calib": f"{x['calib_maps']} maps x {x['calib_B']} vectors",
