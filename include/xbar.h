@@ -63,14 +63,14 @@ typedef enum {
   XBAR_FP64 = 0,
   /* Mixed: diagonal equilibration, FP32 factor and FP32 substitutions, then
    * iterative refinement whose residual r = b - A x and solution update are
-   * computed in FP64. */
+   * computed in float pairs (hi + lo, ~48 significant bits) on the FP32 pipe. */
   XBAR_FP32_IR = 1
 } xbar_precision;
 
 typedef struct {
   int iters;          /* refinement corrections applied (0 for XBAR_FP64) */
   double max_rel_dI;  /* max over (b, j) of |dI| / |I| of the last correction */
-  double resid_inf;   /* max |r| of the last FP64 residual, in amperes (0 for XBAR_FP64) */
+  double resid_inf;   /* max |r| of the last refinement residual, in amperes (0 for XBAR_FP64) */
   double err_est;     /* estimated max relative current error of the result */
   int n_fallback;     /* xbar_surrogate_solve: vectors solved exactly (0 elsewhere) */
 } xbar_solve_info;
@@ -160,8 +160,8 @@ typedef enum {
   XBAR_PHASE_ASSEMBLE = 0,  /* nodal assembly kernels */
   XBAR_PHASE_FACTOR = 1,    /* block Thomas factor kernel */
   XBAR_PHASE_SWEEP = 2,     /* forward/back substitution + current extraction */
-  XBAR_PHASE_RESID = 3,     /* FP64 residual of refinement */
-  XBAR_PHASE_UPDATE = 4,    /* FP64 solution update of refinement */
+  XBAR_PHASE_RESID = 3,     /* residual of refinement (float pairs) */
+  XBAR_PHASE_UPDATE = 4,    /* solution update of refinement (float pairs) */
   XBAR_PHASE_OUTPUT = 5,    /* node-voltage extraction and layout */
   XBAR_NPHASES = 6
 } xbar_phase;
