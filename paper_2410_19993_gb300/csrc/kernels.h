@@ -143,6 +143,27 @@ struct GemmBf16Params {
 // ksplit > 1 splits K over blocks and requires EPI_STORE with atomic = 1 (C zeroed by the caller)
 cudaError_t launch_gemm_bf16(const GemmBf16Params& p, int ksplit, cudaStream_t st);
 
+// ---- surrogate prediction: second and output layers fused with the result (surrogate_infer.cu) ---
+struct SurInferParams {
+  long rows;                        // B * N rows, row r = b*N + j
+  int N;
+  const float* P;                   // [>= N][256]  per-column part of the first layer
+  const float* Q;                   // [>= B][256]  per-vector part of the first layer
+  const float* b1;                  // [256]
+  const struct __nv_bfloat16* W2;   // [256][256] (output unit, input unit)
+  const float* b2;                  // [256]
+  const float* W3;                  // [2][256]
+  const float* b3;                  // [2]
+  const double* Iid;                // [rows] ideal currents
+  const double* Iln;                // [rows] line-model currents
+  double mu, sigma, cal, bound;
+  double* I;                        // [rows] prediction
+  double* est;                      // [rows] relative error estimate (may be NULL)
+  int* flag;                        // [B] set to 1 where an estimate exceeds bound (may be NULL)
+  unsigned* status;
+};
+cudaError_t launch_surrogate_infer(const SurInferParams& p, int nsm, cudaStream_t st);
+
 // ---- FP64 refinement kernels and node voltages ------------------------------------------------
 struct ResidParams {
   int M, Mp, N, B, Bpad;

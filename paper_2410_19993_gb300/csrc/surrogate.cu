@@ -555,22 +555,6 @@ __global__ void f32_to_bf16_rows_kernel(const float* X, long rows, int F, int Fp
   out[idx] = __float2bfloat16_rn(f < F ? X[r * F + f] : 0.0f);
 }
 
-// prediction: I = I_line + I_ideal (mu + sigma n0), relative error estimate
-// c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when any entry of vector b is above the bound
-__global__ void finalize_kernel(const float* out, const float* b3, const double* Iid, const double* Iln, long rows,
-                                double mu, double sigma, double cal, double bound, double* I, double* est, int* flag,
-                                int N) {
-  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  const double ii = Iid[r];
-  const float n0 = out[2 * r] + b3[0], n1 = out[2 * r + 1] + b3[1];
-  const double Ir = Iln[r] + ii * (mu + sigma * (double)n0);
-  const double e = cal * sigma * (double)expf(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
-  I[r] = Ir;
-  if (est) est[r] = e;
-  if (flag && !(e <= bound)) flag[r / N] = 1;
-}
-
 // y <- (y - mu) / sigma
 __global__ void standardise_kernel(float* y, long n, float mu, float inv_sigma) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -599,7 +583,7 @@ struct xbar_surrogate_s {
   int M = 0, N = 0, F = 0, Fp = 0;
   double R[4] = {0, 0, 0, 0};  // R_s, R_w, R_b, R_sense of the circuit the surrogate models
   double gs = 1e-4, vs = 0.5;
-  int dev = 0;
+  int dev = 0, nsm = 1;
   cudaStream_t st = nullptr;
   unsigned* status = nullptr;
   DevArena A;
@@ -681,6 +665,7 @@ extern "C" xbar_status xbar_surrogate_create(int M, int N, double R_s, double R_
   s->passes = line_passes;
   s->st = (cudaStream_t)cuda_stream;
   cudaGetDevice(&s->dev);
+  cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev);
   s->oW1 = 0;
   s->ob1 = s->oW1 + (long)kH * s->Fp;
   s->oW2 = s->ob1 + kH;
@@ -1029,13 +1014,12 @@ extern "C" xbar_status xbar_surrogate_train(xbar_surrogate_t s, int n_maps, cons
 static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, long sGj, int B, const double* V,
                                double* I, double* est, int* flag, double bound) {
   const int M = s->M, N = s->N, Fp = s->Fp;
-  const long rows = (long)B * N, padded = round_up_l(rows, 128);
+  const long rows = (long)B * N;
   const long Npad = round_up_l(N, 128), Bpad = round_up_l(B, 128);
   xbar_status st = map_prep(s, G, sGi, sGj);
   if (st != XBAR_OK) return st;
   XB_CUDA(ensure(s->A, s->Iid, (size_t)rows * 8));
   XB_CUDA(ensure(s->A, s->Iln, (size_t)rows * 8));
-  XB_CUDA(ensure(s->A, s->out, (size_t)rows * 8));
   XB_CUDA(ensure(s->A, s->xgs, (size_t)Npad * Fp * 2));
   XB_CUDA(ensure(s->A, s->xv, (size_t)Bpad * Fp * 2));
   XB_CUDA(ensure(s->A, s->Pm, (size_t)Npad * kH * 4));
@@ -1071,29 +1055,28 @@ static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, lo
   g.A = (const __nv_bfloat16*)s->xv.p;
   g.C = (float*)s->Qm.p;
   XB_CUDA(launch_gemm_bf16(g, 1, s->st));
-  XB_CUDA(cudaMemsetAsync(s->out.p, 0, (size_t)rows * 8, s->st));
-  memset(&g, 0, sizeof(g));
-  g.status = s->status;
-  g.M = (int)padded;
-  g.N = kH;
-  g.K = kH;
-  g.gen_P = (const float*)s->Pm.p;
-  g.gen_Q = (const float*)s->Qm.p;
-  g.gen_bias = s->P + s->ob1;
-  g.gen_N = N;
-  g.gen_valid = rows;
-  g.B = s->W2b;
-  g.sBn = kH;
-  g.sBk = 1;
-  g.mode = GEMM_EPI_HEAD;
-  g.bias = s->P + s->ob2;
-  g.head_W = s->P + s->oW3;
-  g.head_out = (float*)s->out.p;
-  XB_CUDA(launch_gemm_bf16(g, 1, s->st));
-  finalize_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s->st>>>(
-      (const float*)s->out.p, s->P + s->ob3, (const double*)s->Iid.p, (const double*)s->Iln.p, rows, s->mu, s->sigma,
-      s->cal, bound, I, est, flag, N);
-  XB_CUDA(cudaGetLastError());
+  SurInferParams q;
+  memset(&q, 0, sizeof(q));
+  q.rows = rows;
+  q.N = N;
+  q.P = (const float*)s->Pm.p;
+  q.Q = (const float*)s->Qm.p;
+  q.b1 = s->P + s->ob1;
+  q.W2 = s->W2b;
+  q.b2 = s->P + s->ob2;
+  q.W3 = s->P + s->oW3;
+  q.b3 = s->P + s->ob3;
+  q.Iid = (const double*)s->Iid.p;
+  q.Iln = (const double*)s->Iln.p;
+  q.mu = s->mu;
+  q.sigma = s->sigma;
+  q.cal = s->cal;
+  q.bound = bound;
+  q.I = I;
+  q.est = est;
+  q.flag = flag;
+  q.status = s->status;
+  XB_CUDA(launch_surrogate_infer(q, s->nsm, s->st));
   return XBAR_OK;
 }
 

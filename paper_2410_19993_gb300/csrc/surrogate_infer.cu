@@ -1,0 +1,199 @@
+// surrogate_infer.cu -- the surrogate's second and output layers for prediction, with the result
+// formed in the same kernel.
+//
+// Row r = b*N + j (vector b, bit line j).  With the first layer split into a per-column part P_j
+// and a per-vector part Q_b (surrogate.cu), the rest of the network for row r is
+//   h1 = bf16(relu(P_j + Q_b + b1)),  h2 = bf16(relu(W2 h1 + b2)),  n = W3 h2 + b3,
+// and the prediction I = I_line + I_ideal (mu + sigma n0) with the relative error estimate
+// c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when an estimate of vector b is above the bound.
+//
+// Persistent blocks (one per SM, 128 threads): W2 (256 x 256 BF16, 128 KB) is staged once into
+// shared memory as the B operand; each 128-row tile's operand h1 (64 KB) is generated from P, Q
+// and b1 by the threads (thread = row, so a warp's 16-byte stores cover 32 consecutive rows and
+// are bank-conflict free); one thread issues 16 MMAs (M = 128, N = 256, K = 16) into one of two
+// 256-column tensor-memory accumulators; while the tensor core works on tile t, the threads
+// drain tile t-1's accumulator (tcgen05.ld), apply b2, ReLU and the BF16 rounding of h2, reduce
+// against W3 and write the prediction.  Every wait is bounded; on expiry the block records
+// XBAR_DEV_TIMEOUT, waits (bounded) for its own MMAs and frees its tensor memory.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "umma.cuh"
+
+namespace xbar {
+
+namespace si {
+
+constexpr int kH = 256;         // hidden width (K and N of the product)
+constexpr int kRows = 128;      // rows per tile (MMA M)
+constexpr int kThreads = 128;   // thread = tile row
+constexpr uint32_t kLA = (kRows / 8) * 128;  // A: K-direction stride between core matrices (2 KB)
+constexpr uint32_t kLB = (kH / 8) * 128;     // B: same for 256 rows (4 KB)
+constexpr uint32_t kBBytes = (kH / 8) * kLB;    // 128 KB
+constexpr uint32_t kABytes = (kH / 8) * kLA;    // 64 KB
+constexpr size_t kSmem = 1024 + kBBytes + kABytes + (size_t)(2 * kH + 2 * kH) * 4;
+
+__device__ __forceinline__ uint32_t a_off(int m, int g) { return (uint32_t)g * kLA + (uint32_t)(m >> 3) * 128 + (uint32_t)(m & 7) * 16; }
+__device__ __forceinline__ uint32_t b_off(int n, int g) { return (uint32_t)g * kLB + (uint32_t)(n >> 3) * 128 + (uint32_t)(n & 7) * 16; }
+
+}  // namespace si
+
+__global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInferParams p) {
+  using namespace si;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long ntiles = (p.rows + kRows - 1) / kRows;
+
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm);  // [2]: MMA of the tile in accumulator 0 / 1
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 16);
+  unsigned char* Bs = sm + 1024;
+  unsigned char* As = Bs + kBBytes;
+  float* b1s = reinterpret_cast<float*>(As + kABytes);
+  float* b2s = b1s + kH;
+  float* w3s = b2s + kH;  // [2][kH]
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) umma::alloc(tslot, 2 * kH);
+  // W2 (row n = output unit, k = input unit) into the B layout; thread = row, two passes
+  for (int n = tid; n < kH; n += kThreads) {
+    const uint4* src = reinterpret_cast<const uint4*>(p.W2 + (size_t)n * kH);
+#pragma unroll
+    for (int g0 = 0; g0 < kH / 8; g0 += 8) {
+      uint4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = src[g0 + u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) *reinterpret_cast<uint4*>(Bs + b_off(n, g0 + u)) = v[u];
+    }
+  }
+  for (int k = tid; k < kH; k += kThreads) {
+    b1s[k] = p.b1[k];
+    b2s[k] = p.b2[k];
+    w3s[k] = p.W3[k];
+    w3s[kH + k] = p.W3[kH + k];
+  }
+  fence_proxy_async_smem();
+  umma::fence_before();
+  __syncthreads();
+  umma::fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t idesc = umma::idesc_bf16(kRows, kH);
+  const uint64_t adesc = umma::sdesc(smem_addr(As), kLA, 128), bdesc = umma::sdesc(smem_addr(Bs), kLB, 128);
+
+  bool ok = true;
+  int issued = 0;  // tiles whose MMAs this block committed
+  long prev = -1;
+  // drain accumulator `buf` (tile t): b2, ReLU, BF16 rounding, W3, prediction
+  auto epilogue = [&](long t, int buf) {
+    const long r = t * kRows + tid;
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll 1
+    for (int cb = 0; cb < kH; cb += 32) {
+      float a[32];
+      umma::ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kH + cb), a);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(a[q] + b2s[cb + q], 0.0f)));
+        s0 = fmaf(w3s[cb + q], h, s0);
+        s1 = fmaf(w3s[kH + cb + q], h, s1);
+      }
+    }
+    if (r < p.rows) {
+      const double ii = p.Iid[r];
+      const float n0 = s0 + p.b3[0], n1 = s1 + p.b3[1];
+      const double Ir = p.Iln[r] + ii * (p.mu + p.sigma * (double)n0);
+      const double e = p.cal * p.sigma * (double)expf(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
+      p.I[r] = Ir;
+      if (p.est) p.est[r] = e;
+      if (p.flag && !(e <= p.bound)) p.flag[r / p.N] = 1;
+    }
+  };
+
+  for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const int buf = issued & 1;
+    // the previous tile's MMAs read the operand buffer: wait for them before regenerating it
+    if (issued >= 1)
+      ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
+                             XBAR_WAIT_LIMIT_NS, 20);
+    if (__syncthreads_or(!ok)) break;
+    umma::fence_after();
+    {  // operand of tile t: thread = row m
+      const long r = t * kRows + tid;
+      const bool real = r < p.rows;
+      const long b = real ? r / p.N : 0, j = real ? r - b * p.N : 0;
+      const float4* P4 = reinterpret_cast<const float4*>(p.P + j * kH);
+      const float4* Q4 = reinterpret_cast<const float4*>(p.Q + b * kH);
+      const float4* C4 = reinterpret_cast<const float4*>(b1s);
+#pragma unroll
+      for (int g0 = 0; g0 < kH / 8; g0 += 4) {
+        float4 pa[8], qa[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          pa[u] = P4[2 * g0 + u];
+          qa[u] = Q4[2 * g0 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int g = g0 + u;
+          const float4 a0 = pa[2 * u], a1 = pa[2 * u + 1], e0 = qa[2 * u], e1 = qa[2 * u + 1];
+          const float4 c0 = C4[2 * g], c1 = C4[2 * g + 1];
+          const float z[8] = {a0.x + e0.x + c0.x, a0.y + e0.y + c0.y, a0.z + e0.z + c0.z, a0.w + e0.w + c0.w,
+                              a1.x + e1.x + c1.x, a1.y + e1.y + c1.y, a1.z + e1.z + c1.z, a1.w + e1.w + c1.w};
+          alignas(16) __nv_bfloat16 v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(real ? fmaxf(z[e], 0.0f) : 0.0f);
+          *reinterpret_cast<uint4*>(As + a_off(tid, g)) = *reinterpret_cast<const uint4*>(v);
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    umma::fence_before();
+    __syncthreads();  // operand written; the previous epilogue's TMEM reads are done
+    if (tid == 0) {
+      umma::fence_after();
+#pragma unroll
+      for (int s = 0; s < kH / 16; ++s)  // K = 16 per MMA: two core-matrix columns
+        umma::mma_bf16(tbase + (uint32_t)(buf * kH), adesc + (uint64_t)((2 * s * kLA) >> 4),
+                       bdesc + (uint64_t)((2 * s * kLB) >> 4), idesc, s > 0 ? 1u : 0u);
+      umma::commit(&bar[buf]);
+    }
+    ++issued;
+    if (prev >= 0) epilogue(prev, (issued - 2) & 1);  // overlaps the MMAs just issued
+    umma::fence_before();
+    prev = t;
+  }
+  if (ok && prev >= 0) {
+    ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
+                           XBAR_WAIT_LIMIT_NS, 20);
+    ok = !__syncthreads_or(!ok);
+    umma::fence_after();
+    if (ok) epilogue(prev, (issued - 1) & 1);
+  }
+  if (!ok && issued >= 1)  // the last commit covers every MMA of this block: wait for it (bounded)
+    mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 20);
+  umma::fence_before();
+  __syncthreads();
+  if (warp == 0) umma::dealloc(tbase, 2 * kH);
+}
+
+cudaError_t launch_surrogate_infer(const SurInferParams& p, int nsm, cudaStream_t st) {
+  if (p.rows <= 0) return cudaSuccess;
+  if (p.N < 1 || !p.P || !p.Q || !p.W2 || !p.I) return cudaErrorInvalidValue;
+  const long ntiles = (p.rows + si::kRows - 1) / si::kRows;
+  const int grid = (int)std::min<long>(ntiles, nsm > 0 ? nsm : 1);
+  cudaError_t e = cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)si::kSmem);
+  if (e != cudaSuccess) return e;
+  surrogate_infer_kernel<<<grid, si::kThreads, si::kSmem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace xbar
