@@ -110,7 +110,7 @@ cudaError_t launch_sweep_tc_tile(const float* X, float* Xt, int Mp, int N, cudaS
 cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaStream_t st);
 
 // ---- BF16 tensor-core GEMM (gemm_bf16.cu): C[m][n] = sum_k A(m,k) B(n,k) ---------------------
-enum { GEMM_EPI_STORE = 0, GEMM_EPI_BIAS_RELU = 1, GEMM_EPI_MASK = 2, GEMM_EPI_HEAD = 3 };
+enum { GEMM_EPI_STORE = 0, GEMM_EPI_BIAS_RELU = 1, GEMM_EPI_MASK = 2 };
 struct GemmBf16Params {
   int M, N, K;                          // multiples of 128, 128, 64
   const struct __nv_bfloat16* A;        // A(m,k) = A[m*sAm + k*sAk]   (sAk == 1 or sAm == 1)
@@ -126,18 +126,6 @@ struct GemmBf16Params {
   long ldm;
   struct __nv_bfloat16* out;            // BF16 output of EPI_BIAS_RELU / EPI_MASK
   long ldo;
-  // A generated instead of loaded (gen_P != NULL): rows m < gen_valid are
-  //   A(m, k) = bf16(relu(gen_P[(m % gen_N)*K + k] + gen_Q[(m / gen_N)*K + k] + gen_bias[k])),
-  // rows m >= gen_valid are zero
-  const float* gen_P;
-  const float* gen_Q;
-  const float* gen_bias;
-  int gen_N;
-  long gen_valid;
-  // EPI_HEAD: h = bf16(relu(C + bias[n])) and, for rows m < gen_valid,
-  //   head_out[2m + o] += sum over this block's columns n of head_W[o*N + n] h   (o = 0, 1)
-  const float* head_W;
-  float* head_out;
   unsigned* status;
 };
 // ksplit > 1 splits K over blocks and requires EPI_STORE with atomic = 1 (C zeroed by the caller)
