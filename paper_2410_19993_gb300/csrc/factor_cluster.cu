@@ -38,10 +38,10 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 }  // namespace
 
-// dynamic shared memory: rows [R][Mp], pn [R][Mp], D [2][R][R], W [R][R], sigv [Mp], sv [Mp],
-// ev [Mp], sg [2][R], rinv [64]
+// dynamic shared memory: rows [R][Mp], pn [R][Mp], D [R][R], W [R][R], sigv [Mp], sv [Mp],
+// ev [Mp], sg [2][R]
 size_t factor_cluster_smem_bytes(int Mp, int R) {
-  return ((size_t)2 * R * Mp + 3 * (size_t)R * R + 3 * (size_t)Mp + 2 * R + 64) * sizeof(float);
+  return ((size_t)2 * R * Mp + 2 * (size_t)R * R + 3 * (size_t)Mp + 2 * R) * sizeof(float);
 }
 
 // acc[r] (r < 16) += sign * sum_m coef[r*16 + m] * col[m], coefficients read as 16-byte broadcasts
@@ -76,13 +76,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(16) float sm[];
   float* rows = sm;                         // [R][Mp]
   float* pn = rows + (size_t)R * Mp;        // [R][Mp]
-  float* Dm = pn + (size_t)R * Mp;          // [2][R][R]
-  float* W = Dm + 2 * R * R;                // [R][R]
+  float* Dm = pn + (size_t)R * Mp;          // [R][R] inverse of the pivot block
+  float* W = Dm + R * R;                    // [R][R]
   float* sigv = W + R * R;                  // [Mp]
   float* sv = sigv + Mp;                    // [Mp] equilibration scale of column j
   float* ev = sv + Mp;                      // [Mp] coupling to column j-1
   float* sg = ev + Mp;                      // [2][R] sigma of own rows, by step parity
-  float* rinv = sg + 2 * R;                 // [64] pivot reciprocals
 
   if (Mp != C * R || (int)blockDim.x != kThreads) {
     if (tid == 0) set_status(status, XBAR_DEV_BADLAUNCH);
@@ -163,42 +162,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
-    // (4) blocked Gauss-Jordan inversion; panel p = rows of block p
+    // (4) blocked Gauss-Jordan inversion; panel p = rows of block p.
+    // Pivot blocks are inverted in one warp's registers (Gauss-Jordan, no pivoting: the block is
+    // symmetric positive definite).  Lane l holds column l % 16 of rows 8 (l / 16) .. + 7; each
+    // pivot's row, column and diagonal arrive by shuffles.  The owner of panel pp + 1 inverts its
+    // pivot block while panel pp is applied to the rest of its rows (look-ahead), so that only
+    // the first panel of a column step inverts on the critical path.
+    static_assert(R == 16, "register layout assumes 16 x 16 pivot blocks");
+    const int pb = lane & 15, pa0 = (lane >> 4) * 8;
+    auto invert_to_Dm = [&](float (&d)[8]) {  // warp 0
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int qe = q & 7;
+        const float piv = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | q);  // D[q][q]
+        const float ri = __frcp_rn(piv);
+        const float rowq = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | pb);  // D[q][b]
+        float colq[8];  // D[a0 + e][q]
+#pragma unroll
+        for (int e = 0; e < 8; ++e) colq[e] = __shfl_sync(0xffffffffu, d[e], (lane & 16) | q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int a = pa0 + e;
+          float v;
+          if (a == q && pb == q) v = ri;
+          else if (a == q) v = rowq * ri;
+          else if (pb == q) v = -colq[e] * ri;
+          else v = d[e] - colq[e] * rowq * ri;
+          d[e] = v;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) Dm[(pa0 + e) * R + pb] = d[e];
+    };
     for (int pp = 0; pp < C; ++pp) {
       const int P0 = pp * R;
       if ((int)g == pp) {
-        // owner: invert the R x R pivot block in one warp's registers (Gauss-Jordan, no pivoting:
-        // the block is symmetric positive definite).  Lane l holds column l % 16 of rows
-        // 8 (l / 16) .. 8 (l / 16) + 7; each pivot's row, column and diagonal arrive by shuffles,
-        // so the sweep needs no block-wide barrier.
-        static_assert(R == 16, "register layout assumes 16 x 16 pivot blocks");
-        if (warp == 0) {
-          const int b = lane & 15, a0 = (lane >> 4) * 8;
+        if (pp == 0 && warp == 0) {  // later panels were inverted ahead, during the previous update
           float d[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(a0 + e) * Mp + P0 + b];
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const int qe = q & 7;
-            const float piv = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | q);  // D[q][q]
-            const float ri = 1.0f / piv;
-            const float rowq = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | b);  // D[q][b]
-            float colq[8];  // D[a0 + e][q]
-#pragma unroll
-            for (int e = 0; e < 8; ++e) colq[e] = __shfl_sync(0xffffffffu, d[e], (lane & 16) | q);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int a = a0 + e;
-              float v;
-              if (a == q && b == q) v = ri;
-              else if (a == q) v = rowq * ri;
-              else if (b == q) v = -colq[e] * ri;
-              else v = d[e] - colq[e] * rowq * ri;
-              d[e] = v;
-            }
-          }
-#pragma unroll
-          for (int e = 0; e < 8; ++e) Dm[(a0 + e) * R + b] = d[e];
+          for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(pa0 + e) * Mp + P0 + pb];
+          invert_to_Dm(d);
         }
         __syncthreads();
         const float* Dinv = Dm;
@@ -228,18 +231,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4* pub = reinterpret_cast<const float4*>(p.pbuf + (size_t)((j * C + pp) & 1) * R * Mp);
         for (int t = tid; t < R * Mp / 4; t += kThreads) reinterpret_cast<float4*>(pn)[t] = __ldcg(pub + t);
         for (int t = tid; t < R * R; t += kThreads) W[t] = rows[(size_t)(t / R) * Mp + P0 + t % R];
+        const bool ahead = (int)g == pp + 1;  // owner of the next panel: warp 0 inverts ahead
+        const int P1 = P0 + R;
+        float d[8];
+        if (ahead && warp == 0) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(pa0 + e) * Mp + P1 + pb];  // before the update
+        }
         __syncthreads();
-        for (int k = tid; k < Mp; k += kThreads) {
-          float col[R], acc[R];
-          const bool kin = (k >= P0 && k < P0 + R);
+        if (ahead && warp == 0) {
+          // the next pivot block after this panel's update, in the same operation order as the
+          // full update below (so the values are identical), then its inverse
 #pragma unroll
-          for (int m = 0; m < R; ++m) {
-            col[m] = pn[(size_t)m * Mp + k];
-            acc[m] = kin ? 0.0f : rows[(size_t)m * Mp + k];
+          for (int e = 0; e < 8; ++e) {
+            float a = d[e];
+#pragma unroll
+            for (int m = 0; m < R; ++m) a = fmaf(-1.0f * W[(pa0 + e) * R + m], pn[(size_t)m * Mp + P1 + pb], a);
+            d[e] = a;
           }
-          rank16_update(acc, W, col, -1.0f);
+          invert_to_Dm(d);
+        } else {
+          const int t0 = ahead ? tid - 32 : tid, nt = ahead ? kThreads - 32 : kThreads;
+          for (int k = t0; k < Mp; k += nt) {
+            float col[R], acc[R];
+            const bool kin = (k >= P0 && k < P0 + R);
 #pragma unroll
-          for (int r = 0; r < R; ++r) rows[(size_t)r * Mp + k] = acc[r];
+            for (int m = 0; m < R; ++m) {
+              col[m] = pn[(size_t)m * Mp + k];
+              acc[m] = kin ? 0.0f : rows[(size_t)m * Mp + k];
+            }
+            rank16_update(acc, W, col, -1.0f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) rows[(size_t)r * Mp + k] = acc[r];
+          }
         }
         __syncthreads();
       }
