@@ -160,14 +160,18 @@ __device__ __forceinline__ bool epi_sync_or(bool v) {
   return r != 0;
 }
 
-__device__ __forceinline__ int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; }
+__host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; }
 
+// NH = number of 128-row halves of X_j (Mt = 128 NH).  Every size the MMA issue loop touches is a
+// compile-time constant: the single issuing thread then spends no dependent integer work per MMA
+// (runtime offsets in that loop tripled its cost per MMA).
+template <int NH>
 __global__ void __launch_bounds__(tc::kThreads + 32, 1)
-    sweep_tc_kernel(SweepParams<float> p, const float* __restrict__ Xt, int Mt) {
+    sweep_tc_kernel(SweepParams<float> p, const float* __restrict__ Xt) {
   using namespace tc;
   constexpr int BP = kBP, KC = kKC;
-  const int nh = Mt / 128;
-  const int NS = tc_stages(Mt);
+  constexpr int Mt = 128 * NH, nh = NH;
+  constexpr int NS = tc_stages(Mt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b0 = blockIdx.x * BP;
   const int N = p.N, Mp = p.Mp, Bpad = p.Bpad;
@@ -180,21 +184,21 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
   unsigned* fail = reinterpret_cast<unsigned*>(full + 18);
   float* red = reinterpret_cast<float*>(smem + 256);   // [8][64]
   unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
-  const uint32_t part_bytes = (uint32_t)KC * Mt * 4;
-  const uint32_t chunk_bytes = 2 * part_bytes;
+  constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 4;
+  constexpr uint32_t chunk_bytes = 2 * part_bytes;
   unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // (Mt/4) K-blocks of kLBO_B bytes: [hi groups | lo groups]
 
-  const int cps = Mt / KC;  // chunks per step
+  constexpr int cps = Mt / KC;  // chunks per step
   const int nsteps = 2 * N - 1;
   const long long nchunks = (long long)nsteps * cps;
   // accumulators: per 128-row half and per K parity (even/odd K steps, so four independent MMA
   // chains keep the tensor pipe busy), 128 columns [X v_hi | X v_lo] each
-  const uint32_t ncols = (uint32_t)(nh * 4 * BP);
-  const uint32_t idesc2 = idesc_tf32(128, 2 * BP);
-  const uint32_t LBO_A = (uint32_t)Mt * 16, SBO = 128;
+  constexpr uint32_t ncols = (uint32_t)(nh * 4 * BP);
+  constexpr uint32_t idesc2 = idesc_tf32(128, 2 * BP);
+  constexpr uint32_t LBO_A = (uint32_t)Mt * 16, SBO = 128;
 
   if (p.skip && *p.skip) return;  // uniform: before any barrier or tensor-memory allocation
-  if ((int)blockDim.x != kThreads + 32 || (nh != 1 && nh != 2) || b0 + BP > Bpad) {
+  if ((int)blockDim.x != kThreads + 32 || b0 + BP > Bpad) {
     if (tid == 0) set_status(p.status, XBAR_DEV_BADLAUNCH);
     return;
   }
@@ -278,7 +282,8 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
     int mst = 0, muse = 0;
     const uint64_t adesc0 = sdesc(smem_addr(xs), LBO_A, SBO);
     const uint64_t bdesc0 = sdesc(smem_addr(vb), kLBO_B, SBO);
-    const uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_lo = part_bytes >> 4;
+    constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_lo = part_bytes >> 4;
+    uint64_t ast = adesc0;  // descriptor of stage mst
     float local_max = 0.0f;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < N;
@@ -297,23 +302,24 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
         fence_after();
         bool ok = true;
         uint64_t bdesc = bdesc0;  // advances by one K-step (2 K blocks) per chunk
+        uint32_t set = 0;         // column offset of this chunk's K-parity accumulator set
         for (int kc = 0; kc < cps; ++kc) {
           if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t set = (uint32_t)(kc & 1) * (2 * BP);
-          const uint64_t ast = adesc0 + (uint64_t)mst * a_stage;
-          for (int hh = 0; hh < nh; ++hh) {
-            const uint32_t d = tbase + (uint32_t)(hh * 4 * BP) + set;
-            const uint64_t ahi = ast + (uint64_t)hh * a_half;
-            mma_tf32(d, ahi, bdesc, idesc2, kc >= 2 ? 1u : 0u);  // [A_hi v_hi | A_hi v_lo]
-            mma_tf32(d, ahi + a_lo, bdesc, idesc2, 1u);          // + [A_lo v_hi | A_lo v_lo]
+          const uint32_t acc = kc >= 2 ? 1u : 0u, dset = tbase + set;
+#pragma unroll
+          for (int hh = 0; hh < NH; ++hh) {
+            mma_tf32(dset + hh * 4 * BP, ast + hh * a_half, bdesc, idesc2, acc);  // [A_hi v_hi | A_hi v_lo]
+            mma_tf32(dset + hh * 4 * BP, ast + hh * a_half + a_lo, bdesc, idesc2, 1u);  // + [A_lo v_hi | A_lo v_lo]
           }
           mma_commit(&empty[mst]);
           bdesc += (uint64_t)((2 * kLBO_B) >> 4);
-          if (++mst == NS) { mst = 0; ++muse; }
+          set ^= (uint32_t)(2 * BP);
+          ast += a_stage;
+          if (++mst == NS) { mst = 0; ++muse; ast = adesc0; }
         }
         if (ok) {
           mma_commit(dfull);
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
 }
 
 size_t sweep_tc_smem_bytes(int Mt) {
-  const int NS = Mt == 128 ? 8 : 5;
+  const int NS = tc_stages(Mt);
   return 256 + 8 * 64 * 4 + (size_t)NS * (2 * tc::kKC * Mt * 4) + (size_t)(Mt / 4) * tc::kLBO_B;
 }
 
@@ -449,9 +455,10 @@ cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaSt
   const int blocks = (p.B + tc::kBP - 1) / tc::kBP;
   if (blocks == 0) return cudaSuccess;
   const size_t smem = sweep_tc_smem_bytes(Mt);
-  cudaError_t err = cudaFuncSetAttribute(sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = Mt == 128 ? sweep_tc_kernel<1> : sweep_tc_kernel<2>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  sweep_tc_kernel<<<blocks, tc::kThreads + 32, smem, st>>>(p, Xt, Mt);
+  kern<<<blocks, tc::kThreads + 32, smem, st>>>(p, Xt);
   return cudaGetLastError();
 }
 
