@@ -87,7 +87,7 @@ struct SweepParams {
   const T* src;        // [Mp]   initial mode: rhs_0 = src * V_b
   const double* V;     // [B][M] initial mode, else nullptr
   const T* rhs;        // [N][Mp][Bpad] correction mode, else nullptr
-  T* z;                // [N][Mp][Bpad] scratch
+  T* z;                // N * Mp * Bpad scratch, layout private to each sweep kernel
   T* w;                // [N][Mp][Bpad] solution, or nullptr
   double* I;           // [B][N]
   int accumulate;      // 0: I = dI   1: I += dI

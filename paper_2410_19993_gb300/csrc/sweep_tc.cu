@@ -19,6 +19,11 @@
 // same core-matrix order (K-blocks padded by 16 bytes so the stores are bank-conflict free).
 // D = tcgen05 tensor memory, one 64-column slab per 128-row half of X_j.
 //
+// z (the forward result kept for the back substitution) never leaves this kernel, so it is stored
+// in the order the epilogue holds it -- thread = row, four columns per 16-byte access -- as
+// z[j][panel][column/4][row][4]: a warp's access then covers 512 contiguous bytes instead of 32
+// rows 32 KB apart.
+//
 // Roles: a producer warp streams the chunks through a ring of stages (one 1-D bulk copy each,
 // completion on mbarriers) as far ahead as free stages allow; thread 0 issues the MMAs and frees
 // each stage with tcgen05.commit; 8 epilogue warps (named barrier 1, which the producer never
@@ -290,13 +295,19 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
       const int j = fwd ? s : 2 * N - 2 - s;
       const bool nfwd = s + 1 < N;
       // warm L2 with the global operands this step's epilogue will read
-      if (real) {
-        const size_t o = ((size_t)j * Mp + i) * Bpad + b0 + cb;
+      float* zp = p.z + ((size_t)j * (Bpad / BP) + blockIdx.x) * (size_t)Mp * BP;  // z panel of step j
+      {
+        const int i0 = i - lane + (lane & 3) * 8;  // this lane's quarter of the warp's 32 rows
         for (int blk = 0; blk < ncb; ++blk) {
-          if (!fwd) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.z + o + blk * 32));
-          if (nfwd && p.rhs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + o + blk * 32 + (size_t)Mp * Bpad));
+          if (!fwd && i0 < Mp)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(zp + ((size_t)((cb + blk * 32) / 4 + (lane >> 2)) * Mp + i0) * 4));
+          if (real && nfwd && p.rhs)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + ((size_t)(j + 1) * Mp + i) * Bpad + b0 + cb + blk * 32));
         }
       }
+      const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
+                            : 0.0f;
+      const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
       // ---- MMA phase: thread 0 ----------------------------------------------------------------
       if (tid == 0) {
         fence_after();
@@ -339,9 +350,6 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
       fence_after();
 
       const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
-      const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
-                            : 0.0f;
-      const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
       const bool have_w = !fwd || s == N - 1;
       float dots[2];
       for (int blk = 0; blk < ncb; ++blk) {
@@ -358,13 +366,13 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
           }
         }
         const size_t o = rowoff + blk * 32;
+        float4* zrow = reinterpret_cast<float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;  // group stride Mp
         if (fwd) {
           if (real)
-            for (int n = 0; n < 32; n += 4)
-              *reinterpret_cast<float4*>(p.z + o + n) = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
+            for (int n = 0; n < 32; n += 4) zrow[(size_t)(n / 4) * Mp] = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
         } else if (real) {
           for (int n = 0; n < 32; n += 4) {
-            const float4 zz = *reinterpret_cast<const float4*>(p.z + o + n);
+            const float4 zz = zrow[(size_t)(n / 4) * Mp];
             a[n] += zz.x;
             a[n + 1] += zz.y;
             a[n + 2] += zz.z;
