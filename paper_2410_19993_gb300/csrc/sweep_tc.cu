@@ -313,14 +313,15 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
         fence_after();
         bool ok = true;
         uint64_t bdesc = bdesc0;  // advances by one K-step (2 K blocks) per chunk
-        uint32_t set = 0;         // column offset of this chunk's K-parity accumulator set
+        // unrolled by two so that the K-parity accumulator set of each copy is a constant
+#pragma unroll 2
         for (int kc = 0; kc < cps; ++kc) {
           if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t acc = kc >= 2 ? 1u : 0u, dset = tbase + set;
+          const uint32_t acc = kc >= 2 ? 1u : 0u, dset = tbase + (uint32_t)(kc & 1) * (2 * BP);
 #pragma unroll
           for (int hh = 0; hh < NH; ++hh) {
             mma_tf32(dset + hh * 4 * BP, ast + hh * a_half, bdesc, idesc2, acc);  // [A_hi v_hi | A_hi v_lo]
@@ -328,7 +329,6 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
           }
           mma_commit(&empty[mst]);
           bdesc += (uint64_t)((2 * kLBO_B) >> 4);
-          set ^= (uint32_t)(2 * BP);
           ast += a_stage;
           if (++mst == NS) { mst = 0; ++muse; ast = adesc0; }
         }
