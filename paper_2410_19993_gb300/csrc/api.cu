@@ -194,7 +194,9 @@ static xbar_status do_factor(xbar_t h, bool equilibrate, bool upload) {
   if (bpm < 1) bpm = 1;
   XB_CUDA(ensure(h->A, h->X, (size_t)N * Mp * Mp * sizeof(T)));
   XB_CUDA(ensure(h->A, h->fsig, 2 * (size_t)Mp * sizeof(T)));
-  XB_CUDA(ensure(h->A, h->fpbuf, 2 * (size_t)PB * Mp * sizeof(T)));
+  size_t pbuf_n = 2 * (size_t)PB * Mp;
+  if (sizeof(T) == 4 && factor_cluster_supported(Mp)) pbuf_n = std::max(pbuf_n, factor_cluster_pbuf_floats(Mp));
+  XB_CUDA(ensure(h->A, h->fpbuf, pbuf_n * sizeof(T)));
   XB_CUDA(ensure(h->A, h->fbar, 2 * sizeof(unsigned)));
   XB_CUDA(ensure(h->A, h->fparams, sizeof(FactorParams<T>)));
   FactorParams<T> fp;

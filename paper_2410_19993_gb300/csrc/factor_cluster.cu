@@ -4,12 +4,17 @@
 // from the grounded row sums sigma_j), for FP32 factors with 32 <= Mp <= 256.  A cluster of C blocks owns
 // one map; block g holds rows [g R, (g+1) R) of the current matrix in shared memory (R = 16, C = Mp / R).
 // The in-place blocked Gauss-Jordan inversion uses panels of R rows, so panel p is exactly block p's
-// rows: the owner inverts its R x R pivot block, forms the new panel rows and publishes them to a
-// double-buffered global (L2-resident) buffer; one hardware cluster barrier (release/acquire at
-// cluster scope) orders the exchange, and every other block reads the panel from L2 and updates its
-// own rows.  (Pulling the panel from the owner's shared memory instead makes all peers drain one
-// SM's shared-memory port at once and is several times slower.)  One cluster barrier per panel plus
-// one per column step, and no software spin-wait: every block executes the same barrier sequence.
+// rows.  With R_p the owner's rows when panel p starts and D_p^-1 the inverse of their pivot block,
+// Gauss-Jordan replaces the owner's rows by D_p^-1 R_p (D_p^-1 in the pivot columns) and every other
+// block's rows by  row - W' R_p  (-W' in the pivot columns), W' = row[P] D_p^-1.  So the other blocks
+// need only R_p and D_p^-1, not the owner's formed rows: the owner publishes both to its own slot of
+// a global (L2-resident) buffer as soon as they exist and signals each peer's mbarrier (arrive with
+// release at cluster scope; the peer waits with acquire).  The next owner computes its updated pivot
+// block first and inverts it in one warp while its other warps apply the panel (look-ahead), so the
+// chain from panel to panel is signal, L2 read, W', max(update, inversion).  (Pulling panels from the
+// owner's shared memory instead makes all peers drain one SM's shared-memory port at once and is
+// several times slower.)  Every wait is bounded; a block whose wait expires records
+// XBAR_DEV_TIMEOUT and stops waiting but keeps the cluster barrier sequence (one per column step).
 #include <math.h>
 
 #include "common.cuh"
@@ -21,6 +26,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kRows = 16;
+static_assert(kThreads == kRows * kRows, "one thread per element of a pivot block");
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -30,6 +36,39 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// mapa: the shared::cluster address of `local` in block `rank` of this cluster
+__device__ __forceinline__ uint32_t peer_addr(const void* local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(local)), "r"(rank));
+  return r;
+}
+// arrive on a peer block's mbarrier; release at cluster scope orders this block's earlier writes
+__device__ __forceinline__ void arrive_peer(uint32_t bar_cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster_addr) : "memory");
+}
+// bounded wait for phase `parity` of a local mbarrier, acquire at cluster scope
+__device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, unsigned parity, unsigned* status) {
+  auto done = [&]() {
+    uint32_t d;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(d)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return d != 0;
+  };
+  if (done()) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned k = 0;
+  while (!done()) {
+    if ((++k & 255u) == 0 && globaltimer_ns() - t0 > XBAR_WAIT_LIMIT_NS) {
+      set_status(status, XBAR_DEV_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -38,10 +77,16 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 }  // namespace
 
-// dynamic shared memory: rows [R][Mp], pn [R][Mp], D [R][R], W [R][R], sigv [Mp], sv [Mp],
-// ev [Mp], sg [2][R]
+// dynamic shared memory: mbarriers [16], rows [R][Mp], pn [R][Mp], D [R][R], Dr [R][R], W [R][R],
+// Bp [R][R], sigv [Mp], sv [Mp], ev [Mp], sg [2][R]
 size_t factor_cluster_smem_bytes(int Mp, int R) {
-  return ((size_t)2 * R * Mp + 2 * (size_t)R * R + 3 * (size_t)Mp + 2 * R) * sizeof(float);
+  return 16 * sizeof(uint64_t) + ((size_t)2 * R * Mp + 4 * (size_t)R * R + 3 * (size_t)Mp + 2 * R) * sizeof(float);
+}
+
+// global panel slots, one per block of the cluster: R_p [R][Mp] then D_p^-1 [R][R]
+size_t factor_cluster_pbuf_floats(int Mp) {
+  const size_t C = (size_t)Mp / kRows;
+  return C * ((size_t)kRows * Mp + (size_t)kRows * kRows);
 }
 
 // acc[r] (r < 16) += sign * sum_m coef[r*16 + m] * col[m], coefficients read as 16-byte broadcasts
@@ -73,21 +118,32 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = kThreads / 32;
 
-  extern __shared__ __align__(16) float sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);  // [16]: panel p of this column step is ready
+  float* sm = reinterpret_cast<float*>(smraw + 16 * sizeof(uint64_t));
   float* rows = sm;                         // [R][Mp]
-  float* pn = rows + (size_t)R * Mp;        // [R][Mp]
-  float* Dm = pn + (size_t)R * Mp;          // [R][R] inverse of the pivot block
-  float* W = Dm + R * R;                    // [R][R]
-  float* sigv = W + R * R;                  // [Mp]
+  float* pn = rows + (size_t)R * Mp;        // [R][Mp] the current panel's R_p
+  float* Dm = pn + (size_t)R * Mp;          // [R][R] inverse of this block's pivot block
+  float* Dr = Dm + R * R;                   // [R][R] the current panel's D_p^-1
+  float* W = Dr + R * R;                    // [R][R] W' = own rows[P] D_p^-1
+  float* Bp = W + R * R;                    // [R][R] next pivot block (look-ahead)
+  float* sigv = Bp + R * R;                 // [Mp]
   float* sv = sigv + Mp;                    // [Mp] equilibration scale of column j
   float* ev = sv + Mp;                      // [Mp] coupling to column j-1
   float* sg = ev + Mp;                      // [2][R] sigma of own rows, by step parity
 
-  if (Mp != C * R || (int)blockDim.x != kThreads) {
+  if (Mp != C * R || C > 16 || (int)blockDim.x != kThreads) {
     if (tid == 0) set_status(status, XBAR_DEV_BADLAUNCH);
     return;  // uniform across the cluster: every block sees the same arguments
   }
   const float gw = (float)p.gw;
+  if (tid < C) mbar_init(&bars[tid], 1);
+  fence_mbar_init();
+  cluster_sync();  // every block's mbarriers are initialised before any peer arrives on them
+  const size_t slot = (size_t)R * Mp + R * R;  // floats per panel slot
+  __shared__ unsigned failed;                  // a wait of this block expired: stop waiting
+  if (tid == 0) failed = 0;
+  __syncthreads();
 
   for (int j = 0; j < N; ++j) {
     const double* Cj = p.Coff + (size_t)j * Mp * Mp;
@@ -165,47 +221,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     // (4) blocked Gauss-Jordan inversion; panel p = rows of block p.
     // Pivot blocks are inverted in one warp's registers (Gauss-Jordan, no pivoting: the block is
     // symmetric positive definite).  Lane l holds column l % 16 of rows 8 (l / 16) .. + 7; each
-    // pivot's row, column and diagonal arrive by shuffles.  The owner of panel pp + 1 inverts its
-    // pivot block while panel pp is applied to the rest of its rows (look-ahead), so that only
-    // the first panel of a column step inverts on the critical path.
+    // pivot's row, column and diagonal arrive by shuffles.
     static_assert(R == 16, "register layout assumes 16 x 16 pivot blocks");
     const int pb = lane & 15, pa0 = (lane >> 4) * 8;
-    auto invert_to_Dm = [&](float (&d)[8]) {  // warp 0
+    float* myslot = p.pbuf + (size_t)g * slot;  // R_g then D_g^-1
+    auto invert_publish = [&](float (&d)[8]) {  // warp 0: D^-1 to Dm and to this block's slot
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int qe = q & 7;
         const float piv = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | q);  // D[q][q]
-        const float ri = __frcp_rn(piv);
+        const float ri = __fdividef(1.0f, piv);
         const float rowq = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | pb);  // D[q][b]
         float colq[8];  // D[a0 + e][q]
 #pragma unroll
         for (int e = 0; e < 8; ++e) colq[e] = __shfl_sync(0xffffffffu, d[e], (lane & 16) | q);
+        const float rr = rowq * ri;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int a = pa0 + e;
           float v;
           if (a == q && pb == q) v = ri;
-          else if (a == q) v = rowq * ri;
+          else if (a == q) v = rr;
           else if (pb == q) v = -colq[e] * ri;
-          else v = d[e] - colq[e] * rowq * ri;
+          else v = fmaf(-colq[e], rr, d[e]);
           d[e] = v;
         }
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e) Dm[(pa0 + e) * R + pb] = d[e];
+      for (int e = 0; e < 8; ++e) {
+        Dm[(pa0 + e) * R + pb] = d[e];
+        myslot[(size_t)R * Mp + (pa0 + e) * R + pb] = d[e];
+      }
+    };
+    auto signal_peers = [&]() {  // after a __syncthreads that follows every write of the slot
+      if (tid < C && tid != (int)g) arrive_peer(peer_addr(&bars[g], (uint32_t)tid));
     };
     for (int pp = 0; pp < C; ++pp) {
       const int P0 = pp * R;
       if ((int)g == pp) {
-        if (pp == 0 && warp == 0) {  // later panels were inverted ahead, during the previous update
-          float d[8];
+        if (pp == 0) {  // later owners published while applying the previous panel
+          if (warp == 0) {
+            float d[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(pa0 + e) * Mp + P0 + pb];
-          invert_to_Dm(d);
+            for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(pa0 + e) * Mp + P0 + pb];
+            invert_publish(d);
+          }
+          for (int t = tid; t < R * Mp / 4; t += kThreads)
+            reinterpret_cast<float4*>(myslot)[t] = reinterpret_cast<const float4*>(rows)[t];
+          __syncthreads();
+          signal_peers();
         }
-        __syncthreads();
-        const float* Dinv = Dm;
-        // new panel rows: D x (old panel rows) outside the panel columns, D inside
+        // own rows become the panel rows: D^-1 R outside the pivot columns, D^-1 inside
         for (int k = tid; k < Mp; k += kThreads) {
           float col[R], acc[R];
           const bool kin = (k >= P0 && k < P0 + R);
@@ -214,61 +280,75 @@ __global__ void __launch_bounds__(kThreads, 1)
             col[m] = rows[(size_t)m * Mp + k];
             acc[m] = 0.0f;
           }
-          rank16_update(acc, Dinv, col, 1.0f);
-          float* pub = p.pbuf + (size_t)((j * C + pp) & 1) * R * Mp;
+          rank16_update(acc, Dm, col, 1.0f);
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float v = kin ? Dinv[r * R + (k - P0)] : acc[r];
-            rows[(size_t)r * Mp + k] = v;
-            pub[(size_t)r * Mp + k] = v;
-          }
-        }
-      }
-      cluster_sync();  // the owner's new panel rows are visible cluster-wide
-      if ((int)g != pp) {
-        // read the published panel rows (L2) and update own rows:
-        //   row <- (row outside the panel columns) - row[P] . panel
-        const float4* pub = reinterpret_cast<const float4*>(p.pbuf + (size_t)((j * C + pp) & 1) * R * Mp);
-        for (int t = tid; t < R * Mp / 4; t += kThreads) reinterpret_cast<float4*>(pn)[t] = __ldcg(pub + t);
-        for (int t = tid; t < R * R; t += kThreads) W[t] = rows[(size_t)(t / R) * Mp + P0 + t % R];
-        const bool ahead = (int)g == pp + 1;  // owner of the next panel: warp 0 inverts ahead
-        const int P1 = P0 + R;
-        float d[8];
-        if (ahead && warp == 0) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(pa0 + e) * Mp + P1 + pb];  // before the update
+          for (int r = 0; r < R; ++r) rows[(size_t)r * Mp + k] = kin ? Dm[r * R + (k - P0)] : acc[r];
         }
         __syncthreads();
+      } else {
+        // wait for panel pp, then read R_pp and D_pp^-1 from its slot (L2)
+        bool ok = true;
+        if (tid == 0 && !failed) {
+          ok = wait_cluster_bounded(&bars[pp], (unsigned)(j & 1), status);
+          if (!ok) failed = 1;
+        }
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(p.pbuf + (size_t)pp * slot);
+        for (int t = tid; t < R * Mp / 4; t += kThreads) reinterpret_cast<float4*>(pn)[t] = __ldcg(src + t);
+        for (int t = tid; t < R * R / 4; t += kThreads)
+          reinterpret_cast<float4*>(Dr)[t] = __ldcg(src + R * Mp / 4 + t);
+        __syncthreads();
+        {  // W' = own rows[P] D_pp^-1, one element per thread
+          const int a = tid >> 4, bcol = tid & 15;
+          float w = 0.0f;
+#pragma unroll
+          for (int m = 0; m < R; ++m) w = fmaf(rows[(size_t)a * Mp + P0 + m], Dr[m * R + bcol], w);
+          W[tid] = w;
+        }
+        __syncthreads();
+        const bool ahead = (int)g == pp + 1;  // owner of the next panel
+        const int P1 = P0 + R;
+        if (ahead) {  // its pivot block after this panel, same operation order as the update below
+          const int a = tid >> 4, bcol = tid & 15;
+          float v = rows[(size_t)a * Mp + P1 + bcol];
+#pragma unroll
+          for (int m = 0; m < R; ++m) v = fmaf(-1.0f * W[a * R + m], pn[(size_t)m * Mp + P1 + bcol], v);
+          Bp[tid] = v;
+          __syncthreads();
+        }
         if (ahead && warp == 0) {
-          // the next pivot block after this panel's update, in the same operation order as the
-          // full update below (so the values are identical), then its inverse
+          float d[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            float a = d[e];
-#pragma unroll
-            for (int m = 0; m < R; ++m) a = fmaf(-1.0f * W[(pa0 + e) * R + m], pn[(size_t)m * Mp + P1 + pb], a);
-            d[e] = a;
-          }
-          invert_to_Dm(d);
+          for (int e = 0; e < 8; ++e) d[e] = Bp[(pa0 + e) * R + pb];
+          invert_publish(d);
         } else {
+          //   row <- row - W' R_pp outside the pivot columns, -W' inside; the next owner also
+          //   publishes its updated rows as R_{pp+1}
           const int t0 = ahead ? tid - 32 : tid, nt = ahead ? kThreads - 32 : kThreads;
           for (int k = t0; k < Mp; k += nt) {
             float col[R], acc[R];
-            const bool kin = (k >= P0 && k < P0 + R);
+            const bool kin = (k >= P0 && k < P0 + R);  // R_pp holds D there, not D^-1: the result is -W'
 #pragma unroll
             for (int m = 0; m < R; ++m) {
               col[m] = pn[(size_t)m * Mp + k];
-              acc[m] = kin ? 0.0f : rows[(size_t)m * Mp + k];
+              acc[m] = rows[(size_t)m * Mp + k];
             }
             rank16_update(acc, W, col, -1.0f);
 #pragma unroll
-            for (int r = 0; r < R; ++r) rows[(size_t)r * Mp + k] = acc[r];
+            for (int r = 0; r < R; ++r) {
+              if (kin) acc[r] = -W[r * R + (k - P0)];
+              rows[(size_t)r * Mp + k] = acc[r];
+            }
+            if (ahead)
+#pragma unroll
+              for (int r = 0; r < R; ++r) myslot[(size_t)r * Mp + k] = acc[r];
           }
         }
         __syncthreads();
+        if (ahead) signal_peers();
       }
     }
-    cluster_sync();  // every pull of this step's last panel is done before its owner overwrites `rows`
+    cluster_sync();  // every read of this step's slots is done before the next step rewrites them
   }
   {
     float* Xo = p.X + (size_t)(N - 1) * Mp * Mp + (size_t)r0 * Mp;

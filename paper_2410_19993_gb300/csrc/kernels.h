@@ -58,7 +58,7 @@ struct FactorParams {
   const double* e;
   T* X;               // [N][Mp][Mp] output
   T* sig;             // [2][Mp] scratch
-  T* pbuf;            // [2][PB][Mp] scratch
+  T* pbuf;            // scratch: [2][PB][Mp] (factor.cu), factor_cluster_pbuf_floats (factor_cluster.cu)
   unsigned* bar;      // 2 words, zeroed
 };
 
@@ -74,6 +74,7 @@ size_t factor_smem_bytes(int Mp, int rows_per_block);
 // FP32 factor on a thread-block cluster (factor_cluster.cu): 32 <= Mp <= 256
 bool factor_cluster_supported(int Mp);
 int factor_cluster_size(int Mp);
+size_t factor_cluster_pbuf_floats(int Mp);  // panel-slot scratch (FactorParams::pbuf) of one map
 cudaError_t launch_factor_cluster(const FactorParams<float>* maps_dev, int nmaps, int Mp, unsigned* status,
                                   cudaStream_t st);
 
