@@ -24,9 +24,11 @@ namespace xbar {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kWork = 256;             // threads of the row work: one per pivot-block element / column
+constexpr int kInvWarp = kWork / 32;   // one more warp inverts pivot blocks meanwhile
+constexpr int kThreads = kWork + 32;
 constexpr int kRows = 16;
-static_assert(kThreads == kRows * kRows, "one thread per element of a pivot block");
+static_assert(kWork == kRows * kRows, "one thread per element of a pivot block");
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -225,27 +227,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     static_assert(R == 16, "register layout assumes 16 x 16 pivot blocks");
     const int pb = lane & 15, pa0 = (lane >> 4) * 8;
     float* myslot = p.pbuf + (size_t)g * slot;  // R_g then D_g^-1
-    auto invert_publish = [&](float (&d)[8]) {  // warp 0: D^-1 to Dm and to this block's slot
+    auto invert_publish = [&](float (&d)[8]) {  // warp kInvWarp: D^-1 to Dm and to this block's slot
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int qe = q & 7;
-        const float piv = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | q);  // D[q][q]
-        const float ri = __fdividef(1.0f, piv);
-        const float rowq = __shfl_sync(0xffffffffu, d[qe], ((q >> 3) << 4) | pb);  // D[q][b]
-        float colq[8];  // D[a0 + e][q]
+        const int qe = q & 7, qlane = (q >> 3) << 4;
+        const float piv = __shfl_sync(0xffffffffu, d[qe], qlane | q);   // D[q][q]
+        const float rowq = __shfl_sync(0xffffffffu, d[qe], qlane | pb);  // D[q][b]
+        float colq[8];                                                   // D[a0 + e][q]
 #pragma unroll
         for (int e = 0; e < 8; ++e) colq[e] = __shfl_sync(0xffffffffu, d[e], (lane & 16) | q);
-        const float rr = rowq * ri;
+        const float ri = __fdividef(1.0f, piv);
+        // column q: -D[a][q] / piv; elsewhere D[a][b] - D[a][q] D[q][b] / piv; row q: D[q][b] / piv
+        const bool incol = pb == q;
+        const float f = incol ? ri : rowq * ri;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int a = pa0 + e;
-          float v;
-          if (a == q && pb == q) v = ri;
-          else if (a == q) v = rr;
-          else if (pb == q) v = -colq[e] * ri;
-          else v = fmaf(-colq[e], rr, d[e]);
-          d[e] = v;
-        }
+        for (int e = 0; e < 8; ++e) d[e] = fmaf(-colq[e], f, incol ? 0.0f : d[e]);
+        if ((lane & 16) == qlane) d[qe] = f;  // the half-warp holding row q
       }
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -260,19 +257,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int P0 = pp * R;
       if ((int)g == pp) {
         if (pp == 0) {  // later owners published while applying the previous panel
-          if (warp == 0) {
+          if (warp == kInvWarp) {
             float d[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) d[e] = rows[(size_t)(pa0 + e) * Mp + P0 + pb];
             invert_publish(d);
+          } else {
+            for (int t = tid; t < R * Mp / 4; t += kWork)
+              reinterpret_cast<float4*>(myslot)[t] = reinterpret_cast<const float4*>(rows)[t];
           }
-          for (int t = tid; t < R * Mp / 4; t += kThreads)
-            reinterpret_cast<float4*>(myslot)[t] = reinterpret_cast<const float4*>(rows)[t];
           __syncthreads();
           signal_peers();
         }
         // own rows become the panel rows: D^-1 R outside the pivot columns, D^-1 inside
-        for (int k = tid; k < Mp; k += kThreads) {
+        for (int k = tid; k < Mp && tid < kWork; k += kWork) {
           float col[R], acc[R];
           const bool kin = (k >= P0 && k < P0 + R);
 #pragma unroll
@@ -293,30 +291,43 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!ok) failed = 1;
         }
         __syncthreads();
+        // D_pp^-1 to shared memory first; R_pp into registers, stored after W' (its latency overlaps W')
         const float4* src = reinterpret_cast<const float4*>(p.pbuf + (size_t)pp * slot);
-        for (int t = tid; t < R * Mp / 4; t += kThreads) reinterpret_cast<float4*>(pn)[t] = __ldcg(src + t);
-        for (int t = tid; t < R * R / 4; t += kThreads)
-          reinterpret_cast<float4*>(Dr)[t] = __ldcg(src + R * Mp / 4 + t);
+        if (tid < R * R / 4) reinterpret_cast<float4*>(Dr)[tid] = __ldcg(src + R * Mp / 4 + tid);
+        constexpr int kPer = (kRows * 16 * kRows / 4 + kWork - 1) / kWork;  // float4 per thread, Mp <= 16 R
+        float4 rp[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int t = tid + u * kWork;
+          if (tid < kWork && t < R * Mp / 4) rp[u] = __ldcg(src + t);
+        }
         __syncthreads();
-        {  // W' = own rows[P] D_pp^-1, one element per thread
+        if (tid < kWork) {  // W' = own rows[P] D_pp^-1, one element per thread
           const int a = tid >> 4, bcol = tid & 15;
           float w = 0.0f;
 #pragma unroll
           for (int m = 0; m < R; ++m) w = fmaf(rows[(size_t)a * Mp + P0 + m], Dr[m * R + bcol], w);
           W[tid] = w;
+#pragma unroll
+          for (int u = 0; u < kPer; ++u) {
+            const int t = tid + u * kWork;
+            if (t < R * Mp / 4) reinterpret_cast<float4*>(pn)[t] = rp[u];
+          }
         }
         __syncthreads();
         const bool ahead = (int)g == pp + 1;  // owner of the next panel
         const int P1 = P0 + R;
         if (ahead) {  // its pivot block after this panel, same operation order as the update below
-          const int a = tid >> 4, bcol = tid & 15;
-          float v = rows[(size_t)a * Mp + P1 + bcol];
+          if (tid < kWork) {
+            const int a = tid >> 4, bcol = tid & 15;
+            float v = rows[(size_t)a * Mp + P1 + bcol];
 #pragma unroll
-          for (int m = 0; m < R; ++m) v = fmaf(-1.0f * W[a * R + m], pn[(size_t)m * Mp + P1 + bcol], v);
-          Bp[tid] = v;
+            for (int m = 0; m < R; ++m) v = fmaf(-1.0f * W[a * R + m], pn[(size_t)m * Mp + P1 + bcol], v);
+            Bp[tid] = v;
+          }
           __syncthreads();
         }
-        if (ahead && warp == 0) {
+        if (ahead && warp == kInvWarp) {
           float d[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) d[e] = Bp[(pa0 + e) * R + pb];
@@ -324,8 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           //   row <- row - W' R_pp outside the pivot columns, -W' inside; the next owner also
           //   publishes its updated rows as R_{pp+1}
-          const int t0 = ahead ? tid - 32 : tid, nt = ahead ? kThreads - 32 : kThreads;
-          for (int k = t0; k < Mp; k += nt) {
+          for (int k = tid; k < Mp && tid < kWork; k += kWork) {
             float col[R], acc[R];
             const bool kin = (k >= P0 && k < P0 + R);  // R_pp holds D there, not D^-1: the result is -W'
 #pragma unroll
