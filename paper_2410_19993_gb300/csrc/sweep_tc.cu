@@ -25,12 +25,13 @@
 // rows 32 KB apart.
 //
 // Roles: a producer warp streams the chunks through a ring of stages (one 1-D bulk copy each,
-// completion on mbarriers) as far ahead as free stages allow; thread 0 issues the MMAs and frees
-// each stage with tcgen05.commit; 8 epilogue warps (named barrier 1, which the producer never
-// joins) run the epilogue (tcgen05.ld of D, z/w stores,
-// current dot products by warp transpose-reduction, next-step vector split into hi/lo).  Every
-// wait is bounded; on expiry the block records XBAR_DEV_TIMEOUT, drains and frees its tensor
-// memory before returning.
+// completion on mbarriers) as far ahead as free stages allow; one thread of the MMA warp issues
+// the MMAs, frees each stage with tcgen05.commit and signals the finished D; 8 epilogue warps
+// (named barrier 1, which neither of the others joins) drain D from tensor memory, write the next
+// step's vector split into hi/lo and release the next step's MMAs (mbarrier, one arrival per warp)
+// before the work the next step does not need -- z and w stores, current dot products by warp
+// transpose-reduction -- so that this work overlaps the next step's MMAs.  Every wait is bounded;
+// on expiry the block records XBAR_DEV_TIMEOUT, drains and frees its tensor memory before returning.
 #include <math.h>
 #include <string.h>
 
@@ -171,7 +172,7 @@ __host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; 
 // compile-time constant: the single issuing thread then spends no dependent integer work per MMA
 // (runtime offsets in that loop tripled its cost per MMA).
 template <int NH>
-__global__ void __launch_bounds__(tc::kThreads + 32, 1)
+__global__ void __launch_bounds__(tc::kThreads + 64, 1)
     sweep_tc_kernel(SweepParams<float> p, const float* __restrict__ Xt) {
   using namespace tc;
   constexpr int BP = kBP, KC = kKC;
@@ -184,9 +185,10 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);  // [NS]
   uint64_t* empty = full + 8;                          // [NS]
-  uint64_t* dfull = full + 16;                         // [1]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 17);
-  unsigned* fail = reinterpret_cast<unsigned*>(full + 18);
+  uint64_t* dfull = full + 16;                         // [1] D of the step is complete
+  uint64_t* vfull = full + 17;                         // [1] v of the step is written (8 warp arrivals)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 18);
+  unsigned* fail = reinterpret_cast<unsigned*>(full + 19);
   float* red = reinterpret_cast<float*>(smem + 256);   // [8][64]
   unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
   constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 4;
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
   constexpr uint32_t LBO_A = (uint32_t)Mt * 16, SBO = 128;
 
   if (p.skip && *p.skip) return;  // uniform: before any barrier or tensor-memory allocation
-  if ((int)blockDim.x != kThreads + 32 || b0 + BP > Bpad) {
+  if ((int)blockDim.x != kThreads + 64 || b0 + BP > Bpad) {
     if (tid == 0) set_status(p.status, XBAR_DEV_BADLAUNCH);
     return;
   }
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
       mbar_init(&empty[st], 1);
     }
     mbar_init(dfull, 1);
+    mbar_init(vfull, kThreads / 32);
     *fail = 0;
     fence_mbar_init();
   }
@@ -246,76 +249,23 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
         mbar_wait_bounded(&full[c % NS], (unsigned)((c / NS) & 1), p.status, XBAR_WAIT_LIMIT_NS);
     }
     __syncwarp();
-  } else {
-    // ---- 8 epilogue warps; thread 0 also issues the MMAs ---------------------------------------
-    // mapping: warp -> TMEM lane quarter q and either a 128-row half (nh = 2, all 64 columns)
-    // or a 32-column half (nh = 1, rows 0..127)
-    const int q = warp & 3, sub = warp >> 2;
-    const int h = (nh == 2) ? sub : 0;
-    const int cb = (nh == 2) ? 0 : sub * 32;
-    const int ncb = (nh == 2) ? 2 : 1;
-    const int i = h * 128 + q * 32 + lane;
-    const bool real = i < Mp;
-
-    // B-operand byte offset of (node i, column col): K block i/4, N group col/8, row col%8, element i%4
-    unsigned char* vrow = vb + (uint32_t)(i >> 2) * kLBO_B + (uint32_t)(i & 3) * 4;
-    auto put_v = [&](int col, float v) {
-      const float hi = tf32_rna(v);
-      const float lo = tf32_rna(v - hi);
-      unsigned char* a = vrow + (uint32_t)(col >> 3) * 128 + (uint32_t)(col & 7) * 16;
-      *reinterpret_cast<float*>(a) = hi;
-      *reinterpret_cast<float*>(a + (kBP / 8) * 128) = lo;
-    };
-
-    for (int blk = 0; blk < ncb; ++blk)
-      for (int n = 0; n < 32; ++n) {
-        const int col = cb + blk * 32 + n, b = b0 + col;
-        float v = 0.0f;
-        if (p.V) {
-          if (i < p.M && b < p.B) v = p.src[i] * (float)p.V[(size_t)b * p.M + i];
-        } else if (real) {
-          v = p.rhs[(size_t)i * Bpad + b];
-        }
-        put_v(col, v);
-      }
-    fence_proxy_async_smem();
-    fence_before();
-    epi_sync();
-
-    // MMA-issuer state (thread 0): stage ring position and descriptors of every stage/half
-    // (descriptor address fields are the low bits, so stage / half / lo offsets are plain adds)
-    int mst = 0, muse = 0;
-    const uint64_t adesc0 = sdesc(smem_addr(xs), LBO_A, SBO);
-    const uint64_t bdesc0 = sdesc(smem_addr(vb), kLBO_B, SBO);
-    constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_lo = part_bytes >> 4;
-    uint64_t ast = adesc0;  // descriptor of stage mst
-    float local_max = 0.0f;
-    for (int s = 0; s < nsteps; ++s) {
-      const bool fwd = s < N;
-      const int j = fwd ? s : 2 * N - 2 - s;
-      const bool nfwd = s + 1 < N;
-      // warm L2 with the global operands this step's epilogue will read
-      float* zp = p.z + ((size_t)j * (Bpad / BP) + blockIdx.x) * (size_t)Mp * BP;  // z panel of step j
-      {
-        const int i0 = i - lane + (lane & 3) * 8;  // this lane's quarter of the warp's 32 rows
-        for (int blk = 0; blk < ncb; ++blk) {
-          if (!fwd && i0 < Mp)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(zp + ((size_t)((cb + blk * 32) / 4 + (lane >> 2)) * Mp + i0) * 4));
-          if (real && nfwd && p.rhs)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + ((size_t)(j + 1) * Mp + i) * Bpad + b0 + cb + blk * 32));
-        }
-      }
-      const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
-                            : 0.0f;
-      const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
-      // ---- MMA phase: thread 0 ----------------------------------------------------------------
-      if (tid == 0) {
+  } else if (warp == 9) {
+    // ---- MMA issuer: step s starts once the epilogue has written its v (and read step s-1's D) ----
+    if (lane == 0) {
+      // stage ring position and descriptors (descriptor address fields are the low bits, so stage /
+      // half / lo offsets are plain adds)
+      int mst = 0, muse = 0;
+      const uint64_t adesc0 = sdesc(smem_addr(xs), LBO_A, SBO);
+      const uint64_t bdesc0 = sdesc(smem_addr(vb), kLBO_B, SBO);
+      constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_lo = part_bytes >> 4;
+      uint64_t ast = adesc0;  // descriptor of stage mst
+      for (int s = 0; s < nsteps; ++s) {
+        bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, XBAR_WAIT_LIMIT_NS, 0);
         fence_after();
-        bool ok = true;
         uint64_t bdesc = bdesc0;  // advances by one K-step (2 K blocks) per chunk
         // unrolled by two so that the K-parity accumulator set of each copy is a constant
 #pragma unroll 2
-        for (int kc = 0; kc < cps; ++kc) {
+        for (int kc = 0; kc < cps && ok; ++kc) {
           if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
             ok = false;
             break;
@@ -337,10 +287,71 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
         } else {
           *fail = 1;
           mbar_arrive(dfull);  // release the epilogue threads
+          break;
         }
       }
+    }
+    __syncwarp();
+  } else {
+    // ---- 8 epilogue warps --------------------------------------------------------------------
+    // mapping: warp -> TMEM lane quarter q and either a 128-row half (nh = 2, all 64 columns)
+    // or a 32-column half (nh = 1, rows 0..127)
+    const int q = warp & 3, sub = warp >> 2;
+    const int h = (nh == 2) ? sub : 0;
+    const int cb = (nh == 2) ? 0 : sub * 32;
+    constexpr int ncb = (nh == 2) ? 2 : 1;
+    const int i = h * 128 + q * 32 + lane;
+    const bool real = i < Mp;
+
+    // B-operand byte offset of (node i, column col): K block i/4, N group col/8, row col%8, element i%4
+    unsigned char* vrow = vb + (uint32_t)(i >> 2) * kLBO_B + (uint32_t)(i & 3) * 4;
+    auto put_v = [&](int col, float v) {
+      const float hi = tf32_rna(v);
+      const float lo = tf32_rna(v - hi);
+      unsigned char* a = vrow + (uint32_t)(col >> 3) * 128 + (uint32_t)(col & 7) * 16;
+      *reinterpret_cast<float*>(a) = hi;
+      *reinterpret_cast<float*>(a + (kBP / 8) * 128) = lo;
+    };
+    // v written and this thread's reads of D done: release the next step's MMAs (one arrival per warp)
+    auto release_v = [&]() {
+      fence_proxy_async_smem();
+      fence_before();
       __syncwarp();
-      // ---- epilogue ---------------------------------------------------------------------------
+      if (lane == 0) mbar_arrive(vfull);
+    };
+
+    for (int blk = 0; blk < ncb; ++blk)
+      for (int n = 0; n < 32; ++n) {
+        const int col = cb + blk * 32 + n, b = b0 + col;
+        float v = 0.0f;
+        if (p.V) {
+          if (i < p.M && b < p.B) v = p.src[i] * (float)p.V[(size_t)b * p.M + i];
+        } else if (real) {
+          v = p.rhs[(size_t)i * Bpad + b];
+        }
+        put_v(col, v);
+      }
+    release_v();
+
+    float local_max = 0.0f;
+    for (int s = 0; s < nsteps; ++s) {
+      const bool fwd = s < N;
+      const int j = fwd ? s : 2 * N - 2 - s;
+      const bool nfwd = s + 1 < N;
+      // warm L2 with the global operands this step's epilogue will read
+      float* zp = p.z + ((size_t)j * (Bpad / BP) + blockIdx.x) * (size_t)Mp * BP;  // z panel of step j
+      {
+        const int i0 = i - lane + (lane & 3) * 8;  // this lane's quarter of the warp's 32 rows
+        for (int blk = 0; blk < ncb; ++blk) {
+          if (!fwd && i0 < Mp)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(zp + ((size_t)((cb + blk * 32) / 4 + (lane >> 2)) * Mp + i0) * 4));
+          if (real && nfwd && p.rhs)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + ((size_t)(j + 1) * Mp + i) * Bpad + b0 + cb + blk * 32));
+        }
+      }
+      const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
+                            : 0.0f;
+      const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
       // one thread polls the accumulator barrier; the others wait on the named hardware barrier so
       // that no shared-memory polling competes with the tensor core's operand reads
       bool okd = true;
@@ -351,60 +362,77 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
 
       const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
       const bool have_w = !fwd || s == N - 1;
-      float dots[2];
+      // (1) D of this step, both column blocks, and z added in the back substitution
+      float a[ncb][32];
+#pragma unroll
       for (int blk = 0; blk < ncb; ++blk) {
-        float a[32];
-        {
-          float a2[32];
-          const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 4 * BP + cb + blk * 32);
-          tmem_ld32(t0, a);
+        float a2[32];
+        const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 4 * BP + cb + blk * 32);
+        tmem_ld32(t0, a[blk]);
 #pragma unroll
-          for (int part = 1; part < 4; ++part) {  // (even K, v_lo), (odd K, v_hi), (odd K, v_lo)
-            tmem_ld32(t0 + (uint32_t)part * BP, a2);
+        for (int part = 1; part < 4; ++part) {  // (even K, v_lo), (odd K, v_hi), (odd K, v_lo)
+          tmem_ld32(t0 + (uint32_t)part * BP, a2);
 #pragma unroll
-            for (int n = 0; n < 32; ++n) a[n] += a2[n];
-          }
+          for (int n = 0; n < 32; ++n) a[blk][n] += a2[n];
         }
-        const size_t o = rowoff + blk * 32;
-        float4* zrow = reinterpret_cast<float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;  // group stride Mp
-        if (fwd) {
-          if (real)
-            for (int n = 0; n < 32; n += 4) zrow[(size_t)(n / 4) * Mp] = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
-        } else if (real) {
+        if (!fwd && real) {
+          const float4* zrow = reinterpret_cast<const float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;
+#pragma unroll
           for (int n = 0; n < 32; n += 4) {
             const float4 zz = zrow[(size_t)(n / 4) * Mp];
-            a[n] += zz.x;
-            a[n + 1] += zz.y;
-            a[n + 2] += zz.z;
-            a[n + 3] += zz.w;
+            a[blk][n] += zz.x;
+            a[blk][n + 1] += zz.y;
+            a[blk][n + 2] += zz.z;
+            a[blk][n + 3] += zz.w;
           }
         }
-        if (have_w && p.w && real)
-          for (int n = 0; n < 32; n += 4)
-            *reinterpret_cast<float4*>(p.w + o + n) = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
-        if (s + 1 < nsteps) {  // next step's input, split into hi/lo
+      }
+      // (2) the next step's input, split into hi/lo; then the next step's MMAs may start
+      if (s + 1 < nsteps) {
+#pragma unroll
+        for (int blk = 0; blk < ncb; ++blk) {
           if (nfwd && p.rhs && real) {
-            const float* rn = p.rhs + o + (size_t)Mp * Bpad;
+            const float* rn = p.rhs + rowoff + blk * 32 + (size_t)Mp * Bpad;
+#pragma unroll
             for (int n = 0; n < 32; n += 4) {
               const float4 r4 = *reinterpret_cast<const float4*>(rn + n);
-              put_v(cb + blk * 32 + n, fmaf(ej, a[n], r4.x));
-              put_v(cb + blk * 32 + n + 1, fmaf(ej, a[n + 1], r4.y));
-              put_v(cb + blk * 32 + n + 2, fmaf(ej, a[n + 2], r4.z));
-              put_v(cb + blk * 32 + n + 3, fmaf(ej, a[n + 3], r4.w));
+              put_v(cb + blk * 32 + n, fmaf(ej, a[blk][n], r4.x));
+              put_v(cb + blk * 32 + n + 1, fmaf(ej, a[blk][n + 1], r4.y));
+              put_v(cb + blk * 32 + n + 2, fmaf(ej, a[blk][n + 2], r4.z));
+              put_v(cb + blk * 32 + n + 3, fmaf(ej, a[blk][n + 3], r4.w));
             }
           } else {
-            for (int n = 0; n < 32; ++n) put_v(cb + blk * 32 + n, ej * a[n]);
+#pragma unroll
+            for (int n = 0; n < 32; ++n) put_v(cb + blk * 32 + n, ej * a[blk][n]);
           }
         }
+        release_v();
+      }
+      // (3) while the next step's MMAs run: z (forward), w and the current (back substitution)
+      float dots[ncb];
+#pragma unroll
+      for (int blk = 0; blk < ncb; ++blk) {
+        const size_t o = rowoff + blk * 32;
+        if (fwd && real) {
+          float4* zrow = reinterpret_cast<float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;
+#pragma unroll
+          for (int n = 0; n < 32; n += 4)
+            zrow[(size_t)(n / 4) * Mp] = make_float4(a[blk][n], a[blk][n + 1], a[blk][n + 2], a[blk][n + 3]);
+        }
         if (have_w) {
-          for (int n = 0; n < 32; ++n) a[n] *= hj;
-          dots[blk] = transpose_sum32(a, lane);
+          if (p.w && real)
+#pragma unroll
+            for (int n = 0; n < 32; n += 4)
+              *reinterpret_cast<float4*>(p.w + o + n) =
+                  make_float4(a[blk][n], a[blk][n + 1], a[blk][n + 2], a[blk][n + 3]);
+#pragma unroll
+          for (int n = 0; n < 32; ++n) a[blk][n] *= hj;
+          dots[blk] = transpose_sum32(a[blk], lane);
         }
       }
       if (have_w)
+#pragma unroll
         for (int blk = 0; blk < ncb; ++blk) red[warp * 64 + cb + blk * 32 + lane] = dots[blk];
-      fence_proxy_async_smem();
-      fence_before();
       epi_sync();
       if (have_w && tid < BP) {
         float sum = 0.0f;
@@ -434,7 +462,7 @@ __global__ void __launch_bounds__(tc::kThreads + 32, 1)
       if (lane == 0 && local_max > 0.0f) atomic_max_nonneg(p.max_rel, local_max);
     }
   }
-  // ---- teardown: all 9 warps; free tensor memory ------------------------------------------------
+  // ---- teardown: all 10 warps; free tensor memory ------------------------------------------------
   fence_before();
   __syncthreads();
   fence_after();
@@ -466,7 +494,7 @@ cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaSt
   auto kern = Mt == 128 ? sweep_tc_kernel<1> : sweep_tc_kernel<2>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<blocks, tc::kThreads + 32, smem, st>>>(p, Xt);
+  kern<<<blocks, tc::kThreads + 64, smem, st>>>(p, Xt);
   return cudaGetLastError();
 }
 
