@@ -79,10 +79,12 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 }  // namespace
 
-// dynamic shared memory: mbarriers [16], rows [R][Mp], pn [R][Mp], D [R][R], Dr [R][R], W [R][R],
-// Bp [R][R], sigv [Mp], sv [Mp], ev [Mp], sg [2][R]
+// dynamic shared memory: mbarriers [16 panels + 2 staging], rows [R][Mp], pn [R][Mp], D [R][R],
+// Dr [R][R], W [R][R], Bp [R][R], sigv [Mp], sv [Mp], ev [Mp], sg [2][R], then two staging buffers
+// (FP64) of a column step's inputs: C_j own rows [R][Mp], s_j [Mp], s_{j-1} [Mp], e_{j-1} [Mp], h_j own rows [R]
 size_t factor_cluster_smem_bytes(int Mp, int R) {
-  return 16 * sizeof(uint64_t) + ((size_t)2 * R * Mp + 4 * (size_t)R * R + 3 * (size_t)Mp + 2 * R) * sizeof(float);
+  return 18 * sizeof(uint64_t) + ((size_t)2 * R * Mp + 4 * (size_t)R * R + 3 * (size_t)Mp + 2 * R) * sizeof(float) +
+         2 * ((size_t)R * Mp + 3 * (size_t)Mp + R) * sizeof(double);
 }
 
 // global panel slots, one per block of the cluster: R_p [R][Mp] then D_p^-1 [R][R]
@@ -122,7 +124,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   extern __shared__ __align__(16) unsigned char smraw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);  // [16]: panel p of this column step is ready
-  float* sm = reinterpret_cast<float*>(smraw + 16 * sizeof(uint64_t));
+  uint64_t* pbar = bars + 16;                            // [2]: staging buffer b has landed
+  float* sm = reinterpret_cast<float*>(smraw + 18 * sizeof(uint64_t));
   float* rows = sm;                         // [R][Mp]
   float* pn = rows + (size_t)R * Mp;        // [R][Mp] the current panel's R_p
   float* Dm = pn + (size_t)R * Mp;          // [R][R] inverse of this block's pivot block
@@ -133,6 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* sv = sigv + Mp;                    // [Mp] equilibration scale of column j
   float* ev = sv + Mp;                      // [Mp] coupling to column j-1
   float* sg = ev + Mp;                      // [2][R] sigma of own rows, by step parity
+  double* stg = reinterpret_cast<double*>(sg + 2 * R);  // [2] staging buffers (16-byte aligned)
+  const size_t stg_n = (size_t)R * Mp + 3 * (size_t)Mp + R;
 
   if (Mp != C * R || C > 16 || (int)blockDim.x != kThreads) {
     if (tid == 0) set_status(status, XBAR_DEV_BADLAUNCH);
@@ -140,22 +145,50 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   const float gw = (float)p.gw;
   if (tid < C) mbar_init(&bars[tid], 1);
+  if (tid == 0) {
+    mbar_init(&pbar[0], 1);
+    mbar_init(&pbar[1], 1);
+  }
   fence_mbar_init();
   cluster_sync();  // every block's mbarriers are initialised before any peer arrives on them
+  // column step jj's inputs (own rows of C_jj, s_jj, s_jj-1, e_jj-1, own h_jj) -> staging buffer jj & 1
+  // by bulk copies, one step ahead (thread 0)
+  auto stage_inputs = [&](int jj) {
+    double* buf = stg + (size_t)(jj & 1) * stg_n;
+    uint64_t* bar = &pbar[jj & 1];
+    const unsigned cb = (unsigned)(R * Mp * sizeof(double)), vb = (unsigned)(Mp * sizeof(double));
+    const unsigned hb = (unsigned)(R * sizeof(double));
+    unsigned bytes = cb + hb;
+    if (p.s) bytes += vb;
+    if (p.s && jj > 0) bytes += vb;
+    if (jj > 0) bytes += vb;
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(buf, p.Coff + ((size_t)jj * Mp + r0) * Mp, cb, bar);
+    bulk_g2s(buf + (size_t)R * Mp + 3 * Mp, p.h + (size_t)jj * Mp + r0, hb, bar);
+    if (p.s) bulk_g2s(buf + (size_t)R * Mp, p.s + (size_t)jj * Mp, vb, bar);
+    if (p.s && jj > 0) bulk_g2s(buf + (size_t)R * Mp + Mp, p.s + (size_t)(jj - 1) * Mp, vb, bar);
+    if (jj > 0) bulk_g2s(buf + (size_t)R * Mp + 2 * Mp, p.e + (size_t)(jj - 1) * Mp, vb, bar);
+  };
+  if (tid == 0) stage_inputs(0);
   const size_t slot = (size_t)R * Mp + R * R;  // floats per panel slot
   __shared__ unsigned failed;                  // a wait of this block expired: stop waiting
   if (tid == 0) failed = 0;
   __syncthreads();
 
   for (int j = 0; j < N; ++j) {
-    const double* Cj = p.Coff + (size_t)j * Mp * Mp;
-    const double* sj = p.s ? p.s + (size_t)j * Mp : nullptr;
-    const double* sjm = (p.s && j > 0) ? p.s + (size_t)(j - 1) * Mp : nullptr;
-    const double* ejm = j > 0 ? p.e + (size_t)(j - 1) * Mp : nullptr;
-    const double* hj = p.h + (size_t)j * Mp;
-    if (j + 1 < N)  // warm L2 with the next column's off-diagonal block rows of this block
-      for (int t = tid * 16; t < R * Mp; t += kThreads * 16)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(Cj + (size_t)Mp * Mp + (size_t)r0 * Mp + t));
+    // this step's inputs from the staging buffer (the next step's copies overlap this step)
+    const double* stj = stg + (size_t)(j & 1) * stg_n;
+    const double* Cj = stj;                                      // own rows of C_j
+    const double* sj = p.s ? stj + (size_t)R * Mp : nullptr;
+    const double* sjm = (p.s && j > 0) ? stj + (size_t)R * Mp + Mp : nullptr;
+    const double* ejm = j > 0 ? stj + (size_t)R * Mp + 2 * Mp : nullptr;
+    const double* hj = stj + (size_t)R * Mp + 3 * Mp;          // own rows: hj[r] is h_j of row r0 + r
+    if (tid == 0) {
+      if (j + 1 < N) stage_inputs(j + 1);
+      if (!failed && !mbar_wait_bounded(&pbar[j & 1], (unsigned)((j >> 1) & 1), status, XBAR_WAIT_LIMIT_NS))
+        failed = 1;
+    }
+    __syncthreads();
 
     for (int k = tid; k < Mp; k += kThreads) {
       sv[k] = sj ? (float)sj[k] : 1.0f;
@@ -172,12 +205,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = lane; k < Mp; k += 32) acc = fmaf(rows[(size_t)r * Mp + k], sigv[k], acc);
         acc = warp_sum_f(acc);
         if (lane == 0)
-          sg[(j & 1) * R + r] = (i < M) ? (float)hj[i] + gw * (sjm ? (float)sjm[i] : 1.0f) * acc : 0.0f;
+          sg[(j & 1) * R + r] = (i < M) ? (float)hj[r] + gw * (sjm ? (float)sjm[i] : 1.0f) * acc : 0.0f;
       }
     } else {
       for (int r = tid; r < R; r += kThreads) {
         const int i = r0 + r;
-        sg[r] = (i < M) ? (float)(hj[i] + p.gsrc) : 0.0f;
+        sg[r] = (i < M) ? (float)(hj[r] + p.gsrc) : 0.0f;
       }
     }
     __syncthreads();
@@ -192,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // (3) Z^_j own rows: off-diagonal, then the subtraction-free diagonal
     for (int t = tid * 2; t < R * Mp; t += kThreads * 2) {
       const int r = t / Mp, k = t - r * Mp, i = r0 + r;
-      const double2 c2 = *reinterpret_cast<const double2*>(Cj + (size_t)r0 * Mp + t);
+      const double2 c2 = *reinterpret_cast<const double2*>(Cj + t);
       const float si = sv[i], ei = ev[i];
       const float x0 = j > 0 ? rows[t] : 0.0f, x1 = j > 0 ? rows[t + 1] : 0.0f;  // X^_{j-1}
       float v0 = 0.0f, v1 = 0.0f;
