@@ -14,7 +14,7 @@
 //
 // Operands.  A = X_j, split and pre-tiled in global memory (sweep_tc_tile_kernel) in the
 // no-swizzle K-major core-matrix order of the MMA (8 rows x 16 bytes per core matrix), chunk by
-// chunk of 16 K-elements, hi and lo adjacent, so one 1-D bulk copy per chunk lands MMA-ready data
+// chunk of 8 K-elements (one MMA K step), hi and lo adjacent, so one 1-D bulk copy per chunk lands MMA-ready data
 // in shared memory.  B = the running vector of the panel, written by the epilogue threads into the
 // same core-matrix order (K-blocks padded by 16 bytes so the stores are bank-conflict free).
 // D = tcgen05 tensor memory, one 64-column slab per 128-row half of X_j.
@@ -134,8 +134,8 @@ __device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane) {
 }  // namespace tc
 
 // X_j (FP32 [N][Mp][Mp]) -> split TF32 hi/lo in the MMA's chunked core-matrix order
-// Xt[j][kc][part][cl][g][r][e], kc < Mt/16, part 0 = hi / 1 = lo, cl < 4, g < Mt/8, r < 8, e < 4;
-// element (row n, column k) of X_j with n = 8g + r, k = 16 kc + 4 cl + e; rows/cols >= Mp are zero.
+// Xt[j][kc][part][cl][g][r][e], kc < Mt/8, part 0 = hi / 1 = lo, cl < 2, g < Mt/8, r < 8, e < 4;
+// element (row n, column k) of X_j with n = 8g + r, k = 8 kc + 4 cl + e; rows/cols >= Mp are zero.
 __global__ void sweep_tc_tile_kernel(const float* __restrict__ X, float* __restrict__ Xt, int Mp, int Mt, int N) {
   const size_t per = (size_t)Mt * Mt;
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
