@@ -225,9 +225,8 @@ static xbar_status do_factor(xbar_t h, bool equilibrate, bool upload) {
     XB_CUDA(launch_factor<T>((const FactorParams<T>*)h->fparams.p, 1, Mp, bpm, h->status, h->st));
   h->tc_ready = 0;
   if (sizeof(T) == 4 && use_tc_sweep(h)) {
-    const int Mt = sweep_tc_rows(Mp);
-    XB_CUDA(ensure(h->A, h->Xt, (size_t)N * Mt * Mt * 2 * sizeof(float)));
-    XB_CUDA(launch_sweep_tc_tile((const float*)h->X.p, (float*)h->Xt.p, Mp, N, h->st));
+    XB_CUDA(ensure(h->A, h->Xt, sweep_tc_tile_bytes(Mp, N)));
+    XB_CUDA(launch_sweep_tc_tile((const float*)h->X.p, h->Xt.p, Mp, N, h->st));
     h->tc_ready = 1;
   }
   return XBAR_OK;
@@ -415,7 +414,7 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     sp.status = h->status;
     {
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
-      if (tc) XB_CUDA(launch_sweep_tc(sp, (const float*)h->Xt.p, st));  // x0 = solve32(b)
+      if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, st));  // x0 = solve32(b)
       else XB_CUDA(launch_sweep<float>(sp, st));
     }
     {
@@ -438,7 +437,7 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       sp.max_rel = (float*)h->maxrel.p;
       {
         PhaseScope ps(h, XBAR_PHASE_SWEEP);     // dhat = solve32(rhat), I += dI
-        if (tc) XB_CUDA(launch_sweep_tc(sp, (const float*)h->Xt.p, st));
+        if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, st));
         else XB_CUDA(launch_sweep<float>(sp, st));
       }
       w_current = false;
@@ -552,7 +551,7 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   sp.V = dV; sp.rhs = nullptr; sp.z = (float*)h->z.p; sp.w = (float*)h->dhat.p; sp.I = dI;
   sp.accumulate = 0; sp.max_rel = nullptr; sp.status = h->status;
   auto sweep = [&]() -> cudaError_t {
-    return tc ? launch_sweep_tc(sp, (const float*)h->Xt.p, st) : launch_sweep<float>(sp, st);
+    return tc ? launch_sweep_tc(sp, h->Xt.p, st) : launch_sweep<float>(sp, st);
   };
   XB_CUDA(launch_ir_init(state, st));
   XB_CUDA(sweep());                      // x0 = solve32(b)

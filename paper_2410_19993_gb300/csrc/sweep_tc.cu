@@ -4,20 +4,20 @@
 //     z_0 = X_0 r_0,  z_j = X_j (r_j + e_{j-1} o z_{j-1});   w_{N-1} = z_{N-1},
 //     w_j = z_j + X_j (e_j o w_{j+1});   I_j = hs_j . w_j,
 // for a panel of 64 input vectors per block.  Each step is D[Mt x 64] = X_j[Mt x Mt] . v[Mt x 64]
-// computed from split TF32 operands (x = x_hi + x_lo, both TF32): with B_hi and B_lo stacked along
-// N, each K step issues A_hi [B_hi | B_lo] and A_lo [B_hi | B_lo] (N = 128) and the epilogue adds
-// the two column halves, so D = (A_hi + A_lo)(B_hi + B_lo) with FP32 accumulation in tensor memory,
-// which keeps FP32-level accuracy: a plain TF32 product would cost the refinement several extra
-// FP64 residual passes.  Dependent accumulations into one TMEM region serialise at ~170 cycles
-// per MMA, so even and odd K steps accumulate into separate regions: 2 row halves x 2 K parities
-// = 4 independent chains.
+// computed from three-term BF16 splits (x = x0 + x1 + x2, each BF16: together 24+ significant bits,
+// FP32-level accuracy; a plain BF16 or TF32 product would cost the refinement extra passes).  With
+// v0 | v1 | v2 stacked along N, each K step of 16 issues A0 [v0 v1 v2] (N = 192), A1 [v0 v1]
+// (N = 128) and A2 [v0] (N = 64) into one FP32 accumulator, and the epilogue adds its three column
+// blocks: (A0 + A1 + A2)(v0 + v1 + v2) without A1 v2, A2 v1, A2 v2 (each below 2^-26 relative).
+// Against a split-TF32 product (x = hi + lo, four K=8 products per 16 K) this moves 6 instead of
+// 8 bytes per element of X_j, issues 96 instead of 128 MMAs per step and does 25% less tensor work.
 //
 // Operands.  A = X_j, split and pre-tiled in global memory (sweep_tc_tile_kernel) in the
 // no-swizzle K-major core-matrix order of the MMA (8 rows x 16 bytes per core matrix), chunk by
-// chunk of 8 K-elements (one MMA K step), hi and lo adjacent, so one 1-D bulk copy per chunk lands MMA-ready data
-// in shared memory.  B = the running vector of the panel, written by the epilogue threads into the
-// same core-matrix order (K-blocks padded by 16 bytes so the stores are bank-conflict free).
-// D = tcgen05 tensor memory, one 64-column slab per 128-row half of X_j.
+// chunk of 16 K-elements (one MMA K step), the three parts adjacent, so one 1-D bulk copy per chunk
+// lands MMA-ready data in shared memory.  B = the running vector of the panel, written by the
+// epilogue threads into the same core-matrix order (K-blocks padded by 16 bytes so the stores are
+// bank-conflict free).  D = tcgen05 tensor memory, one 192-column slab per 128-row half of X_j.
 //
 // z (the forward result kept for the back substitution) never leaves this kernel, so it is stored
 // in the order the epilogue holds it -- thread = row, four columns per 16-byte access -- as
@@ -32,22 +32,26 @@
 // before the work the next step does not need -- z and w stores, current dot products by warp
 // transpose-reduction -- so that this work overlaps the next step's MMAs.  Every wait is bounded;
 // on expiry the block records XBAR_DEV_TIMEOUT, drains and frees its tensor memory before returning.
+#include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "umma.cuh"
 
 namespace xbar {
 
 namespace tc {
 
-constexpr int kBP = 64;       // input vectors per panel (MMA N)
-constexpr int kKC = 8;        // K elements per bulk-copied chunk (one MMA K step)
+constexpr int kBP = 64;       // input vectors per panel
+constexpr int kKC = 16;       // K elements per bulk-copied chunk (one BF16 MMA K step)
+constexpr int kParts = 3;     // x = x0 + x1 + x2
 constexpr int kThreads = 256;
-// B operand = [v_hi | v_lo] stacked along N (16 core-matrix groups of 8 columns per K block); the
-// 16-byte pad between K blocks keeps the epilogue's stores bank-conflict free
-constexpr uint32_t kLBO_B = 2 * (kBP / 8) * 128 + 16;
+// B operand = [v0 | v1 | v2] stacked along N (24 core-matrix groups of 8 columns per K block of 8
+// nodes); the 16-byte pad between K blocks keeps the epilogue's stores bank-conflict free
+constexpr uint32_t kLBO_B = kParts * (kBP / 8) * 128 + 16;
+constexpr int kDCols = kParts * kBP;  // accumulator columns per 128-row half
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
@@ -63,14 +67,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_addr(bar))
@@ -78,20 +74,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-// no-swizzle K-major shared-memory matrix descriptor (tcgen05 format: version 1 in bits 46-47)
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // 32 consecutive 32-bit TMEM columns of this thread's lane
@@ -110,10 +92,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// x = x0 + x1 + x2 + O(2^-27 |x|), each term BF16 rounded to nearest (the differences are exact in FP32)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& x0, __nv_bfloat16& x1, __nv_bfloat16& x2) {
+  x0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(x0);
+  x1 = __float2bfloat16_rn(r1);
+  x2 = __float2bfloat16_rn(r1 - __bfloat162float(x1));
 }
 
 // sum over the 32 lanes of column `lane` of v[0..31] (v is destroyed)
@@ -133,10 +117,11 @@ __device__ __forceinline__ float transpose_sum32(float (&v)[32], int lane) {
 
 }  // namespace tc
 
-// X_j (FP32 [N][Mp][Mp]) -> split TF32 hi/lo in the MMA's chunked core-matrix order
-// Xt[j][kc][part][cl][g][r][e], kc < Mt/8, part 0 = hi / 1 = lo, cl < 2, g < Mt/8, r < 8, e < 4;
-// element (row n, column k) of X_j with n = 8g + r, k = 8 kc + 4 cl + e; rows/cols >= Mp are zero.
-__global__ void sweep_tc_tile_kernel(const float* __restrict__ X, float* __restrict__ Xt, int Mp, int Mt, int N) {
+// X_j (FP32 [N][Mp][Mp]) -> three-term BF16 split in the MMA's chunked core-matrix order
+// Xt[j][kc][part][kcol][g][r][e], kc < Mt/16, part < 3, kcol < 2, g < Mt/8, r < 8, e < 8;
+// element (row n, column k) of X_j with n = 8g + r, k = 16 kc + 8 kcol + e; rows/cols >= Mp are zero.
+__global__ void sweep_tc_tile_kernel(const float* __restrict__ X, __nv_bfloat16* __restrict__ Xt, int Mp, int Mt,
+                                     int N) {
   const size_t per = (size_t)Mt * Mt;
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx >= per * N) return;
@@ -144,14 +129,15 @@ __global__ void sweep_tc_tile_kernel(const float* __restrict__ X, float* __restr
   const int rem = (int)(idx - (size_t)j * per);
   const int n = rem / Mt, k = rem - n * Mt;
   const float x = (n < Mp && k < Mp) ? X[((size_t)j * Mp + n) * Mp + k] : 0.0f;
-  const float hi = tc::tf32_rna(x);
-  const float lo = tc::tf32_rna(x - hi);
-  const int kc = k / tc::kKC, kl = k % tc::kKC, cl = kl / 4, e = kl % 4, g = n / 8, r = n % 8;
-  const size_t part = (size_t)(tc::kKC / 4) * (Mt / 8) * 32;  // floats in one part of a chunk
-  const size_t base = ((size_t)j * (Mt / tc::kKC) + kc) * 2 * part;
-  const size_t off = ((size_t)cl * (Mt / 8) + g) * 32 + r * 4 + e;
-  Xt[base + off] = hi;
-  Xt[base + part + off] = lo;
+  __nv_bfloat16 x0, x1, x2;
+  tc::split3(x, x0, x1, x2);
+  const int kc = k / tc::kKC, kk = k % tc::kKC, kcol = kk / 8, e = kk % 8, g = n / 8, r = n % 8;
+  const size_t part = (size_t)2 * (Mt / 8) * 64;  // elements in one part of a chunk
+  const size_t base = ((size_t)j * (Mt / tc::kKC) + kc) * tc::kParts * part;
+  const size_t off = ((size_t)kcol * (Mt / 8) + g) * 64 + r * 8 + e;
+  Xt[base + off] = x0;
+  Xt[base + part + off] = x1;
+  Xt[base + 2 * part + off] = x2;
 }
 
 // named barrier over the 8 epilogue warps (the producer warp never joins it)
@@ -173,7 +159,7 @@ __host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; 
 // (runtime offsets in that loop tripled its cost per MMA).
 template <int NH>
 __global__ void __launch_bounds__(tc::kThreads + 64, 1)
-    sweep_tc_kernel(SweepParams<float> p, const float* __restrict__ Xt) {
+    sweep_tc_kernel(SweepParams<float> p, const __nv_bfloat16* __restrict__ Xt) {
   using namespace tc;
   constexpr int BP = kBP, KC = kKC;
   constexpr int Mt = 128 * NH, nh = NH;
@@ -191,18 +177,19 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   unsigned* fail = reinterpret_cast<unsigned*>(full + 19);
   float* red = reinterpret_cast<float*>(smem + 256);   // [8][64]
   unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
-  constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 4;
-  constexpr uint32_t chunk_bytes = 2 * part_bytes;
-  unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // (Mt/4) K-blocks of kLBO_B bytes: [hi groups | lo groups]
+  constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 2;  // one BF16 part of a chunk
+  constexpr uint32_t chunk_bytes = kParts * part_bytes;
+  unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // (Mt/8) K-blocks of kLBO_B bytes: [v0 | v1 | v2 groups]
 
   constexpr int cps = Mt / KC;  // chunks per step
   const int nsteps = 2 * N - 1;
   const long long nchunks = (long long)nsteps * cps;
-  // accumulators: per 128-row half and per K parity (even/odd K steps, so four independent MMA
-  // chains keep the tensor pipe busy), 128 columns [X v_hi | X v_lo] each
-  constexpr uint32_t ncols = (uint32_t)(nh * 4 * BP);
-  constexpr uint32_t idesc2 = idesc_tf32(128, 2 * BP);
-  constexpr uint32_t LBO_A = (uint32_t)Mt * 16, SBO = 128;
+  // accumulators: per 128-row half, 192 columns [X v0 | X v1 | X v2] (tensor memory is allocated in
+  // powers of two)
+  constexpr uint32_t ncols = nh == 2 ? 512u : 256u;
+  constexpr uint32_t id192 = umma::idesc_bf16(128, 3 * BP), id128 = umma::idesc_bf16(128, 2 * BP),
+                     id64 = umma::idesc_bf16(128, BP);
+  constexpr uint32_t LBO_A = (uint32_t)(Mt / 8) * 128, SBO = 128;
 
   if (p.skip && *p.skip) return;  // uniform: before any barrier or tensor-memory allocation
   if ((int)blockDim.x != kThreads + 64 || b0 + BP > Bpad) {
@@ -239,7 +226,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
         issued = c + 1;
         const int j = s < N ? s : 2 * N - 2 - s;
         mbar_arrive_expect_tx(&full[st], chunk_bytes);
-        bulk_g2s(xs + (size_t)st * chunk_bytes, Xt + ((size_t)j * cps + kc) * (chunk_bytes / 4), chunk_bytes,
+        bulk_g2s(xs + (size_t)st * chunk_bytes, Xt + ((size_t)j * cps + kc) * (chunk_bytes / 2), chunk_bytes,
                  &full[st]);
         if (++kc == cps) { kc = 0; ++s; }
         if (++st == NS) { st = 0; ++use; }
@@ -255,28 +242,30 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       // stage ring position and descriptors (descriptor address fields are the low bits, so stage /
       // half / lo offsets are plain adds)
       int mst = 0, muse = 0;
-      const uint64_t adesc0 = sdesc(smem_addr(xs), LBO_A, SBO);
-      const uint64_t bdesc0 = sdesc(smem_addr(vb), kLBO_B, SBO);
-      constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_lo = part_bytes >> 4;
+      const uint64_t adesc0 = umma::sdesc(smem_addr(xs), LBO_A, SBO);
+      const uint64_t bdesc0 = umma::sdesc(smem_addr(vb), kLBO_B, SBO);
+      constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_part = part_bytes >> 4;
       uint64_t ast = adesc0;  // descriptor of stage mst
       for (int s = 0; s < nsteps; ++s) {
         bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, XBAR_WAIT_LIMIT_NS, 0);
         fence_after();
         uint64_t bdesc = bdesc0;  // advances by one K-step (2 K blocks) per chunk
-        // unrolled by two so that the K-parity accumulator set of each copy is a constant
-#pragma unroll 2
         for (int kc = 0; kc < cps && ok; ++kc) {
           if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t acc = kc >= 2 ? 1u : 0u, dset = tbase + (uint32_t)(kc & 1) * (2 * BP);
+          const uint32_t acc = kc > 0 ? 1u : 0u;
 #pragma unroll
-          for (int hh = 0; hh < NH; ++hh) {
-            mma_tf32(dset + hh * 4 * BP, ast + hh * a_half, bdesc, idesc2, acc);  // [A_hi v_hi | A_hi v_lo]
-            mma_tf32(dset + hh * 4 * BP, ast + hh * a_half + a_lo, bdesc, idesc2, 1u);  // + [A_lo v_hi | A_lo v_lo]
-          }
+          for (int hh = 0; hh < NH; ++hh)  // A0 [v0 v1 v2]
+            umma::mma_bf16(tbase + hh * kDCols, ast + hh * a_half, bdesc, id192, acc);
+#pragma unroll
+          for (int hh = 0; hh < NH; ++hh)  // + A1 [v0 v1]
+            umma::mma_bf16(tbase + hh * kDCols, ast + a_part + hh * a_half, bdesc, id128, 1u);
+#pragma unroll
+          for (int hh = 0; hh < NH; ++hh)  // + A2 [v0]
+            umma::mma_bf16(tbase + hh * kDCols, ast + 2 * a_part + hh * a_half, bdesc, id64, 1u);
           mma_commit(&empty[mst]);
           bdesc += (uint64_t)((2 * kLBO_B) >> 4);
           ast += a_stage;
@@ -303,14 +292,16 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
     const int i = h * 128 + q * 32 + lane;
     const bool real = i < Mp;
 
-    // B-operand byte offset of (node i, column col): K block i/4, N group col/8, row col%8, element i%4
-    unsigned char* vrow = vb + (uint32_t)(i >> 2) * kLBO_B + (uint32_t)(i & 3) * 4;
+    // B-operand byte offset of (node i, column col): K block i/8, N group col/8, row col%8, element i%8;
+    // part p of the split is column col + 64 p
+    unsigned char* vrow = vb + (uint32_t)(i >> 3) * kLBO_B + (uint32_t)(i & 7) * 2;
     auto put_v = [&](int col, float v) {
-      const float hi = tf32_rna(v);
-      const float lo = tf32_rna(v - hi);
+      __nv_bfloat16 x0, x1, x2;
+      split3(v, x0, x1, x2);
       unsigned char* a = vrow + (uint32_t)(col >> 3) * 128 + (uint32_t)(col & 7) * 16;
-      *reinterpret_cast<float*>(a) = hi;
-      *reinterpret_cast<float*>(a + (kBP / 8) * 128) = lo;
+      *reinterpret_cast<__nv_bfloat16*>(a) = x0;
+      *reinterpret_cast<__nv_bfloat16*>(a + (kBP / 8) * 128) = x1;
+      *reinterpret_cast<__nv_bfloat16*>(a + 2 * (kBP / 8) * 128) = x2;
     };
     // v written and this thread's reads of D done: release the next step's MMAs (one arrival per warp)
     auto release_v = [&]() {
@@ -367,10 +358,10 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 #pragma unroll
       for (int blk = 0; blk < ncb; ++blk) {
         float a2[32];
-        const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 4 * BP + cb + blk * 32);
+        const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kDCols + cb + blk * 32);
         tmem_ld32(t0, a[blk]);
 #pragma unroll
-        for (int part = 1; part < 4; ++part) {  // (even K, v_lo), (odd K, v_hi), (odd K, v_lo)
+        for (int part = 1; part < kParts; ++part) {  // the X v1 and X v2 column blocks
           tmem_ld32(t0 + (uint32_t)part * BP, a2);
 #pragma unroll
           for (int n = 0; n < 32; ++n) a[blk][n] += a2[n];
@@ -471,21 +462,27 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 
 size_t sweep_tc_smem_bytes(int Mt) {
   const int NS = tc_stages(Mt);
-  return 256 + 8 * 64 * 4 + (size_t)NS * (2 * tc::kKC * Mt * 4) + (size_t)(Mt / 4) * tc::kLBO_B;
+  return 256 + 8 * 64 * 4 + (size_t)NS * (tc::kParts * tc::kKC * Mt * 2) + (size_t)(Mt / 8) * tc::kLBO_B;
 }
 
 bool sweep_tc_supported(int Mp) { return Mp <= 256; }
 
 int sweep_tc_rows(int Mp) { return Mp <= 128 ? 128 : 256; }
 
-cudaError_t launch_sweep_tc_tile(const float* X, float* Xt, int Mp, int N, cudaStream_t st) {
+size_t sweep_tc_tile_bytes(int Mp, int N) {
+  const int Mt = sweep_tc_rows(Mp);
+  return (size_t)N * Mt * Mt * tc::kParts * sizeof(__nv_bfloat16);
+}
+
+cudaError_t launch_sweep_tc_tile(const float* X, void* Xt, int Mp, int N, cudaStream_t st) {
   const int Mt = sweep_tc_rows(Mp);
   const size_t n = (size_t)Mt * Mt * N;
-  sweep_tc_tile_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, Xt, Mp, Mt, N);
+  sweep_tc_tile_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, static_cast<__nv_bfloat16*>(Xt), Mp, Mt,
+                                                                    N);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaStream_t st) {
+cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, cudaStream_t st) {
   const int Mt = sweep_tc_rows(p.Mp);
   if (p.Bp != tc::kBP || p.Bpad % tc::kBP) return cudaErrorInvalidValue;
   const int blocks = (p.B + tc::kBP - 1) / tc::kBP;
@@ -494,7 +491,7 @@ cudaError_t launch_sweep_tc(const SweepParams<float>& p, const float* Xt, cudaSt
   auto kern = Mt == 128 ? sweep_tc_kernel<1> : sweep_tc_kernel<2>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<blocks, tc::kThreads + 64, smem, st>>>(p, Xt);
+  kern<<<blocks, tc::kThreads + 64, smem, st>>>(p, static_cast<const __nv_bfloat16*>(Xt));
   return cudaGetLastError();
 }
 
