@@ -16,8 +16,9 @@
 // no-swizzle K-major core-matrix order of the MMA (8 rows x 16 bytes per core matrix), chunk by
 // chunk of 16 K-elements (one MMA K step), the three parts adjacent, so one 1-D bulk copy per chunk
 // lands MMA-ready data in shared memory.  B = the running vector of the panel, written by the
-// epilogue threads into the same core-matrix order (K-blocks padded by 16 bytes so the stores are
-// bank-conflict free).  D = tcgen05 tensor memory, one 192-column slab per 128-row half of X_j.
+// epilogue threads in MN-major core-matrix order (8 nodes x 8 columns per core matrix, columns
+// contiguous), so each thread stores 8 columns of its node at once.  D = tcgen05 tensor memory,
+// one 192-column slab per 128-row half of X_j.
 //
 // z (the forward result kept for the back substitution) never leaves this kernel, so it is stored
 // in the order the epilogue holds it -- thread = row, four columns per 16-byte access -- as
@@ -48,9 +49,10 @@ constexpr int kBP = 64;       // input vectors per panel
 constexpr int kKC = 16;       // K elements per bulk-copied chunk (one BF16 MMA K step)
 constexpr int kParts = 3;     // x = x0 + x1 + x2
 constexpr int kThreads = 256;
-// B operand = [v0 | v1 | v2] stacked along N (24 core-matrix groups of 8 columns per K block of 8
-// nodes); the 16-byte pad between K blocks keeps the epilogue's stores bank-conflict free
-constexpr uint32_t kLBO_B = kParts * (kBP / 8) * 128 + 16;
+// B operand = [v0 | v1 | v2] stacked along N (24 groups of 8 columns), MN-major: a core matrix is 8
+// nodes x 8 consecutive columns (16 bytes), so a thread (= node) writes 8 columns per 16-byte store;
+// node groups of 8 are 128 bytes apart, column groups (Mt/8)*128 bytes apart
+__host__ __device__ constexpr uint32_t lbo_b(int Mt) { return (uint32_t)(Mt / 8) * 128; }  // column-group stride
 constexpr int kDCols = kParts * kBP;  // accumulator columns per 128-row half
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -179,7 +181,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
   constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 2;  // one BF16 part of a chunk
   constexpr uint32_t chunk_bytes = kParts * part_bytes;
-  unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // (Mt/8) K-blocks of kLBO_B bytes: [v0 | v1 | v2 groups]
+  unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // 24 column groups of lbo_b(Mt) bytes: [v0 | v1 | v2]
+  constexpr uint32_t LBO_B = lbo_b(Mt);
 
   constexpr int cps = Mt / KC;  // chunks per step
   const int nsteps = 2 * N - 1;
@@ -187,8 +190,9 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   // accumulators: per 128-row half, 192 columns [X v0 | X v1 | X v2] (tensor memory is allocated in
   // powers of two)
   constexpr uint32_t ncols = nh == 2 ? 512u : 256u;
-  constexpr uint32_t id192 = umma::idesc_bf16(128, 3 * BP), id128 = umma::idesc_bf16(128, 2 * BP),
-                     id64 = umma::idesc_bf16(128, BP);
+  constexpr uint32_t kBMajorMN = 1u << 16;  // instruction descriptor: B is MN-major
+  constexpr uint32_t id192 = umma::idesc_bf16(128, 3 * BP) | kBMajorMN,
+                     id128 = umma::idesc_bf16(128, 2 * BP) | kBMajorMN, id64 = umma::idesc_bf16(128, BP) | kBMajorMN;
   constexpr uint32_t LBO_A = (uint32_t)(Mt / 8) * 128, SBO = 128;
 
   if (p.skip && *p.skip) return;  // uniform: before any barrier or tensor-memory allocation
@@ -243,13 +247,15 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       // half / lo offsets are plain adds)
       int mst = 0, muse = 0;
       const uint64_t adesc0 = umma::sdesc(smem_addr(xs), LBO_A, SBO);
-      const uint64_t bdesc0 = umma::sdesc(smem_addr(vb), kLBO_B, SBO);
+      // MN-major, no swizzle: the descriptor's leading byte offset is the stride between groups of
+      // 8 nodes (K), the stride byte offset the stride between groups of 8 columns (N)
+      const uint64_t bdesc0 = umma::sdesc(smem_addr(vb), 128, LBO_B);
       constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_part = part_bytes >> 4;
       uint64_t ast = adesc0;  // descriptor of stage mst
       for (int s = 0; s < nsteps; ++s) {
         bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, XBAR_WAIT_LIMIT_NS, 0);
         fence_after();
-        uint64_t bdesc = bdesc0;  // advances by one K-step (2 K blocks) per chunk
+        uint64_t bdesc = bdesc0;  // advances by one K-step (2 node groups of 128 bytes) per chunk
         for (int kc = 0; kc < cps && ok; ++kc) {
           if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
             ok = false;
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
           for (int hh = 0; hh < NH; ++hh)  // + A2 [v0]
             umma::mma_bf16(tbase + hh * kDCols, ast + 2 * a_part + hh * a_half, bdesc, id64, 1u);
           mma_commit(&empty[mst]);
-          bdesc += (uint64_t)((2 * kLBO_B) >> 4);
+          bdesc += (uint64_t)((2 * 128) >> 4);
           ast += a_stage;
           if (++mst == NS) { mst = 0; ++muse; ast = adesc0; }
         }
@@ -292,16 +298,26 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
     const int i = h * 128 + q * 32 + lane;
     const bool real = i < Mp;
 
-    // B-operand byte offset of (node i, column col): K block i/8, N group col/8, row col%8, element i%8;
-    // part p of the split is column col + 64 p
-    unsigned char* vrow = vb + (uint32_t)(i >> 3) * kLBO_B + (uint32_t)(i & 7) * 2;
-    auto put_v = [&](int col, float v) {
-      __nv_bfloat16 x0, x1, x2;
-      split3(v, x0, x1, x2);
-      unsigned char* a = vrow + (uint32_t)(col >> 3) * 128 + (uint32_t)(col & 7) * 16;
-      *reinterpret_cast<__nv_bfloat16*>(a) = x0;
-      *reinterpret_cast<__nv_bfloat16*>(a + (kBP / 8) * 128) = x1;
-      *reinterpret_cast<__nv_bfloat16*>(a + 2 * (kBP / 8) * 128) = x2;
+    // B-operand byte offset of (node i, column n): column group n/8 (LBO_B apart), node group i/8
+    // (128 bytes apart), node i%8 (16 bytes), column n%8 (2 bytes); part p of the split is column
+    // col + 64 p.  Columns col0 .. col0+7 (col0 % 8 == 0) of this node, three 16-byte stores.
+    unsigned char* vrow = vb + (uint32_t)(i >> 3) * 128 + (uint32_t)(i & 7) * 16;
+    auto put_v8 = [&](int col0, const float (&v)[8]) {
+      uint32_t w[3][4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {  // the split of split3, two columns per conversion
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[e], v[e + 1]);
+        const float ra = v[e] - __low2float(h0), rb = v[e + 1] - __high2float(h0);
+        const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - __low2float(h1), rb - __high2float(h1));
+        w[0][e / 2] = *reinterpret_cast<const uint32_t*>(&h0);
+        w[1][e / 2] = *reinterpret_cast<const uint32_t*>(&h1);
+        w[2][e / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      unsigned char* a = vrow + (uint32_t)(col0 >> 3) * LBO_B;
+#pragma unroll
+      for (int q2 = 0; q2 < 3; ++q2)
+        *reinterpret_cast<uint4*>(a + (uint32_t)q2 * (kBP / 8) * LBO_B) = make_uint4(w[q2][0], w[q2][1], w[q2][2], w[q2][3]);
     };
     // v written and this thread's reads of D done: release the next step's MMAs (one arrival per warp)
     auto release_v = [&]() {
@@ -312,15 +328,18 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
     };
 
     for (int blk = 0; blk < ncb; ++blk)
-      for (int n = 0; n < 32; ++n) {
-        const int col = cb + blk * 32 + n, b = b0 + col;
-        float v = 0.0f;
-        if (p.V) {
-          if (i < p.M && b < p.B) v = p.src[i] * (float)p.V[(size_t)b * p.M + i];
-        } else if (real) {
-          v = p.rhs[(size_t)i * Bpad + b];
+      for (int n0 = 0; n0 < 32; n0 += 8) {
+        float v[8];
+        for (int e = 0; e < 8; ++e) {
+          const int b = b0 + cb + blk * 32 + n0 + e;
+          v[e] = 0.0f;
+          if (p.V) {
+            if (i < p.M && b < p.B) v[e] = p.src[i] * (float)p.V[(size_t)b * p.M + i];
+          } else if (real) {
+            v[e] = p.rhs[(size_t)i * Bpad + b];
+          }
         }
-        put_v(col, v);
+        put_v8(cb + blk * 32 + n0, v);
       }
     release_v();
 
@@ -385,16 +404,23 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
           if (nfwd && p.rhs && real) {
             const float* rn = p.rhs + rowoff + blk * 32 + (size_t)Mp * Bpad;
 #pragma unroll
-            for (int n = 0; n < 32; n += 4) {
+            for (int n = 0; n < 32; n += 8) {
               const float4 r4 = *reinterpret_cast<const float4*>(rn + n);
-              put_v(cb + blk * 32 + n, fmaf(ej, a[blk][n], r4.x));
-              put_v(cb + blk * 32 + n + 1, fmaf(ej, a[blk][n + 1], r4.y));
-              put_v(cb + blk * 32 + n + 2, fmaf(ej, a[blk][n + 2], r4.z));
-              put_v(cb + blk * 32 + n + 3, fmaf(ej, a[blk][n + 3], r4.w));
+              const float4 r5 = *reinterpret_cast<const float4*>(rn + n + 4);
+              const float v[8] = {fmaf(ej, a[blk][n], r4.x),     fmaf(ej, a[blk][n + 1], r4.y),
+                                  fmaf(ej, a[blk][n + 2], r4.z), fmaf(ej, a[blk][n + 3], r4.w),
+                                  fmaf(ej, a[blk][n + 4], r5.x), fmaf(ej, a[blk][n + 5], r5.y),
+                                  fmaf(ej, a[blk][n + 6], r5.z), fmaf(ej, a[blk][n + 7], r5.w)};
+              put_v8(cb + blk * 32 + n, v);
             }
           } else {
 #pragma unroll
-            for (int n = 0; n < 32; ++n) put_v(cb + blk * 32 + n, ej * a[blk][n]);
+            for (int n = 0; n < 32; n += 8) {
+              float v[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[e] = ej * a[blk][n + e];
+              put_v8(cb + blk * 32 + n, v);
+            }
           }
         }
         release_v();
@@ -462,7 +488,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 
 size_t sweep_tc_smem_bytes(int Mt) {
   const int NS = tc_stages(Mt);
-  return 256 + 8 * 64 * 4 + (size_t)NS * (tc::kParts * tc::kKC * Mt * 2) + (size_t)(Mt / 8) * tc::kLBO_B;
+  return 256 + 8 * 64 * 4 + (size_t)NS * (tc::kParts * tc::kKC * Mt * 2) + (size_t)tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt);
 }
 
 bool sweep_tc_supported(int Mp) { return Mp <= 256; }
