@@ -295,9 +295,9 @@ def run_xbar(args):
         bound, peak, note = "alu", peaks["fp64_tflops"], "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock"
     traffic, traffic_note = None, None
     if dom == "sweep" and (M, N) == (256, 256) and bound == "tensor":
-        # ncu DRAM read + write of one sweep_tc_kernel launch at B = 2048 (2.346 GB), scaled by
+        # ncu DRAM read + write of one sweep_tc_kernel launch at B = 2048 (2.280 GB), scaled by
         # the vectors of this launch: the kernel's streams are per vector
-        traffic = 2.346e9 * B / 2048
+        traffic = 2.280e9 * B / 2048
         traffic_note = "ncu dram__bytes_read+write at B=2048 scaled by B (profiles/sweep_tc_xbar256_B2048.md)"
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note, "peak_note": note,
