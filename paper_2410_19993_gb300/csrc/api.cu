@@ -161,6 +161,13 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   return XBAR_OK;
 }
 
+// BF16 terms of the tensor-core sweep for refinement correction `it` (0-based).  A correction
+// only needs accuracy relative to its own size, so the first two are solved with two terms
+// (~2^-17 per product); one term (2^-9 per product, accumulated over the 2N - 1 dependent steps)
+// proved too coarse to certify convergence.  Any later correction (slow convergence) and the
+// initial solve use all three (FP32-level accuracy).
+static int correction_terms(int it) { return it < 2 ? 2 : 3; }
+
 // Kernel variants.  FP32 substitutions run on the tensor cores (sweep_tc.cu) when the block fits
 // (Mp <= 256) and FP32 factors on a thread-block cluster (factor_cluster.cu) when 32 <= Mp <= 256,
 // unless the handle's options (xbar_set_option, set by the batch autotuner) or the environment
@@ -414,7 +421,7 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     sp.status = h->status;
     {
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
-      if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, st));  // x0 = solve32(b)
+      if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, 3, st));  // x0 = solve32(b)
       else XB_CUDA(launch_sweep<float>(sp, st));
     }
     {
@@ -437,7 +444,7 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       sp.max_rel = (float*)h->maxrel.p;
       {
         PhaseScope ps(h, XBAR_PHASE_SWEEP);     // dhat = solve32(rhat), I += dI
-        if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, st));
+        if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, correction_terms(it), st));
         else XB_CUDA(launch_sweep<float>(sp, st));
       }
       w_current = false;
@@ -550,11 +557,11 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   sp.X = (const float*)h->X.p; sp.e = m.e32; sp.hs = m.hs32; sp.src = m.src32;
   sp.V = dV; sp.rhs = nullptr; sp.z = (float*)h->z.p; sp.w = (float*)h->dhat.p; sp.I = dI;
   sp.accumulate = 0; sp.max_rel = nullptr; sp.status = h->status;
-  auto sweep = [&]() -> cudaError_t {
-    return tc ? launch_sweep_tc(sp, h->Xt.p, st) : launch_sweep<float>(sp, st);
+  auto sweep = [&](int terms) -> cudaError_t {
+    return tc ? launch_sweep_tc(sp, h->Xt.p, terms, st) : launch_sweep<float>(sp, st);
   };
   XB_CUDA(launch_ir_init(state, st));
-  XB_CUDA(sweep());                      // x0 = solve32(b)
+  XB_CUDA(sweep(3));                     // x0 = solve32(b)
   XB_CUDA(launch_update(rp, 1, st));     // w = s o dhat, I = h . w
   sp.V = nullptr;
   sp.rhs = (const float*)h->rhat.p;
@@ -564,7 +571,7 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   rp.skip = &state->done;
   for (int it = 0; it < max_iter; ++it) {
     XB_CUDA(launch_resid(rp, st));       // rhat = s o (b - A w)   [FP64]  (skipped once converged)
-    XB_CUDA(sweep());                    // dhat = solve32(rhat), I += dI
+    XB_CUDA(sweep(correction_terms(it)));  // dhat = solve32(rhat), I += dI
     XB_CUDA(launch_ir_check(state, tol, st));
     XB_CUDA(launch_update(rp, 0, st));   // w += s o dhat, I = h . w   (skipped once converged)
   }

@@ -109,7 +109,8 @@ constexpr int kSweepTcPanel = 64;
 // X (FP32 [N][Mp][Mp]) -> Xt: three-term BF16 split in the MMA's chunked core-matrix order
 size_t sweep_tc_tile_bytes(int Mp, int N);
 cudaError_t launch_sweep_tc_tile(const float* X, void* Xt, int Mp, int N, cudaStream_t st);
-cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, cudaStream_t st);
+// terms = leading BF16 terms of the split used (1..3): 3 gives FP32-level accuracy
+cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, int terms, cudaStream_t st);
 
 // ---- BF16 tensor-core GEMM (gemm_bf16.cu): C[m][n] = sum_k A(m,k) B(n,k) ---------------------
 enum { GEMM_EPI_STORE = 0, GEMM_EPI_BIAS_RELU = 1, GEMM_EPI_MASK = 2 };

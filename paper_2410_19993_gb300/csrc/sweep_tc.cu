@@ -53,7 +53,10 @@ constexpr int kThreads = 256;
 // nodes x 8 consecutive columns (16 bytes), so a thread (= node) writes 8 columns per 16-byte store;
 // node groups of 8 are 128 bytes apart, column groups (Mt/8)*128 bytes apart
 __host__ __device__ constexpr uint32_t lbo_b(int Mt) { return (uint32_t)(Mt / 8) * 128; }  // column-group stride
-constexpr int kDCols = kParts * kBP;  // accumulator columns per 128-row half
+// tensor-memory columns for NH halves of KP * 64 columns (allocations are powers of two >= 32)
+__host__ __device__ constexpr uint32_t tmem_cols(int NH, int KP) {
+  return NH * KP * kBP <= 64 ? 64u : NH * KP * kBP <= 128 ? 128u : NH * KP * kBP <= 256 ? 256u : 512u;
+}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
@@ -156,10 +159,12 @@ __device__ __forceinline__ bool epi_sync_or(bool v) {
 
 __host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; }
 
-// NH = number of 128-row halves of X_j (Mt = 128 NH).  Every size the MMA issue loop touches is a
-// compile-time constant: the single issuing thread then spends no dependent integer work per MMA
-// (runtime offsets in that loop tripled its cost per MMA).
-template <int NH>
+// NH = number of 128-row halves of X_j (Mt = 128 NH); KP = number of BF16 terms of the split used
+// (1..3; the tiles always hold three, a sweep with fewer copies and multiplies only the leading
+// ones).  Every size the MMA issue loop touches is a compile-time constant: the single issuing
+// thread then spends no dependent integer work per MMA (runtime offsets in that loop tripled its
+// cost per MMA).
+template <int NH, int KP>
 __global__ void __launch_bounds__(tc::kThreads + 64, 1)
     sweep_tc_kernel(SweepParams<float> p, const __nv_bfloat16* __restrict__ Xt) {
   using namespace tc;
@@ -187,12 +192,12 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   constexpr int cps = Mt / KC;  // chunks per step
   const int nsteps = 2 * N - 1;
   const long long nchunks = (long long)nsteps * cps;
-  // accumulators: per 128-row half, 192 columns [X v0 | X v1 | X v2] (tensor memory is allocated in
+  // accumulators: per 128-row half, KP * 64 columns [X v0 | X v1 | X v2] (tensor memory is allocated in
   // powers of two)
-  constexpr uint32_t ncols = nh == 2 ? 512u : 256u;
-  constexpr uint32_t kBMajorMN = 1u << 16;  // instruction descriptor: B is MN-major
-  constexpr uint32_t id192 = umma::idesc_bf16(128, 3 * BP) | kBMajorMN,
-                     id128 = umma::idesc_bf16(128, 2 * BP) | kBMajorMN, id64 = umma::idesc_bf16(128, BP) | kBMajorMN;
+  constexpr uint32_t ncols = tmem_cols(NH, KP);
+  constexpr int dcols = KP * BP;
+  constexpr uint32_t copy_bytes = KP * part_bytes;  // leading KP terms of each chunk
+  constexpr uint32_t kBMajorMN = 1u << 16;          // instruction descriptor: B is MN-major
   constexpr uint32_t LBO_A = (uint32_t)(Mt / 8) * 128, SBO = 128;
 
   if (p.skip && *p.skip) return;  // uniform: before any barrier or tensor-memory allocation
@@ -229,8 +234,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
           break;
         issued = c + 1;
         const int j = s < N ? s : 2 * N - 2 - s;
-        mbar_arrive_expect_tx(&full[st], chunk_bytes);
-        bulk_g2s(xs + (size_t)st * chunk_bytes, Xt + ((size_t)j * cps + kc) * (chunk_bytes / 2), chunk_bytes,
+        mbar_arrive_expect_tx(&full[st], copy_bytes);
+        bulk_g2s(xs + (size_t)st * chunk_bytes, Xt + ((size_t)j * cps + kc) * (chunk_bytes / 2), copy_bytes,
                  &full[st]);
         if (++kc == cps) { kc = 0; ++s; }
         if (++st == NS) { st = 0; ++use; }
@@ -264,14 +269,11 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
           fence_after();
           const uint32_t acc = kc > 0 ? 1u : 0u;
 #pragma unroll
-          for (int hh = 0; hh < NH; ++hh)  // A0 [v0 v1 v2]
-            umma::mma_bf16(tbase + hh * kDCols, ast + hh * a_half, bdesc, id192, acc);
+          for (int pt = 0; pt < KP; ++pt)  // A_pt [v_0 .. v_(KP-1-pt)]: A0 [v0 v1 v2], A1 [v0 v1], A2 [v0]
 #pragma unroll
-          for (int hh = 0; hh < NH; ++hh)  // + A1 [v0 v1]
-            umma::mma_bf16(tbase + hh * kDCols, ast + a_part + hh * a_half, bdesc, id128, 1u);
-#pragma unroll
-          for (int hh = 0; hh < NH; ++hh)  // + A2 [v0]
-            umma::mma_bf16(tbase + hh * kDCols, ast + 2 * a_part + hh * a_half, bdesc, id64, 1u);
+            for (int hh = 0; hh < NH; ++hh)
+              umma::mma_bf16(tbase + hh * dcols, ast + pt * a_part + hh * a_half, bdesc,
+                             umma::idesc_bf16(128, BP * (KP - pt)) | kBMajorMN, pt == 0 ? acc : 1u);
           mma_commit(&empty[mst]);
           bdesc += (uint64_t)((2 * 128) >> 4);
           ast += a_stage;
@@ -305,18 +307,22 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
     auto put_v8 = [&](int col0, const float (&v)[8]) {
       uint32_t w[3][4];
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {  // the split of split3, two columns per conversion
+      for (int e = 0; e < 8; e += 2) {  // the split of split3 (leading KP terms), two columns per conversion
         const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[e], v[e + 1]);
-        const float ra = v[e] - __low2float(h0), rb = v[e + 1] - __high2float(h0);
-        const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - __low2float(h1), rb - __high2float(h1));
         w[0][e / 2] = *reinterpret_cast<const uint32_t*>(&h0);
-        w[1][e / 2] = *reinterpret_cast<const uint32_t*>(&h1);
-        w[2][e / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+        if (KP > 1) {
+          const float ra = v[e] - __low2float(h0), rb = v[e + 1] - __high2float(h0);
+          const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
+          w[1][e / 2] = *reinterpret_cast<const uint32_t*>(&h1);
+          if (KP > 2) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - __low2float(h1), rb - __high2float(h1));
+            w[2][e / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+        }
       }
       unsigned char* a = vrow + (uint32_t)(col0 >> 3) * LBO_B;
 #pragma unroll
-      for (int q2 = 0; q2 < 3; ++q2)
+      for (int q2 = 0; q2 < KP; ++q2)
         *reinterpret_cast<uint4*>(a + (uint32_t)q2 * (kBP / 8) * LBO_B) = make_uint4(w[q2][0], w[q2][1], w[q2][2], w[q2][3]);
     };
     // v written and this thread's reads of D done: release the next step's MMAs (one arrival per warp)
@@ -377,10 +383,10 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 #pragma unroll
       for (int blk = 0; blk < ncb; ++blk) {
         float a2[32];
-        const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kDCols + cb + blk * 32);
+        const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * dcols + cb + blk * 32);
         tmem_ld32(t0, a[blk]);
 #pragma unroll
-        for (int part = 1; part < kParts; ++part) {  // the X v1 and X v2 column blocks
+        for (int part = 1; part < KP; ++part) {  // the X v1 and X v2 column blocks
           tmem_ld32(t0 + (uint32_t)part * BP, a2);
 #pragma unroll
           for (int n = 0; n < 32; ++n) a[blk][n] += a2[n];
@@ -508,13 +514,17 @@ cudaError_t launch_sweep_tc_tile(const float* X, void* Xt, int Mp, int N, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, cudaStream_t st) {
+cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, int terms, cudaStream_t st) {
   const int Mt = sweep_tc_rows(p.Mp);
   if (p.Bp != tc::kBP || p.Bpad % tc::kBP) return cudaErrorInvalidValue;
   const int blocks = (p.B + tc::kBP - 1) / tc::kBP;
   if (blocks == 0) return cudaSuccess;
   const size_t smem = sweep_tc_smem_bytes(Mt);
-  auto kern = Mt == 128 ? sweep_tc_kernel<1> : sweep_tc_kernel<2>;
+  if (terms < 1 || terms > tc::kParts) return cudaErrorInvalidValue;
+  using Kern = void (*)(SweepParams<float>, const __nv_bfloat16*);
+  const Kern kerns[2][3] = {{sweep_tc_kernel<1, 1>, sweep_tc_kernel<1, 2>, sweep_tc_kernel<1, 3>},
+                            {sweep_tc_kernel<2, 1>, sweep_tc_kernel<2, 2>, sweep_tc_kernel<2, 3>}};
+  const Kern kern = kerns[Mt == 128 ? 0 : 1][terms - 1];
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<blocks, tc::kThreads + 64, smem, st>>>(p, static_cast<const __nv_bfloat16*>(Xt));
