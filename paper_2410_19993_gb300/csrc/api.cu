@@ -419,12 +419,19 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     sp.accumulate = 0;
     sp.max_rel = nullptr;
     sp.status = h->status;
-    {
+    if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 as float pairs itself
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
-      if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, 3, st));  // x0 = solve32(b)
-      else XB_CUDA(launch_sweep<float>(sp, st));
-    }
-    {
+      sp.w = nullptr;
+      sp.w2out = rp.w2;
+      sp.s32 = m.s32;
+      XB_CUDA(launch_sweep_tc(sp, h->Xt.p, 3, st));
+      sp.w = (float*)h->dhat.p;
+      sp.w2out = nullptr;
+    } else {
+      {
+        PhaseScope ps(h, XBAR_PHASE_SWEEP);
+        XB_CUDA(launch_sweep<float>(sp, st));  // x0 = solve32(b)
+      }
       PhaseScope ps(h, XBAR_PHASE_UPDATE);
       XB_CUDA(launch_update(rp, 1, st));        // w = s o dhat, I = h . w
     }
@@ -561,8 +568,17 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
     return tc ? launch_sweep_tc(sp, h->Xt.p, terms, st) : launch_sweep<float>(sp, st);
   };
   XB_CUDA(launch_ir_init(state, st));
-  XB_CUDA(sweep(3));                     // x0 = solve32(b)
-  XB_CUDA(launch_update(rp, 1, st));     // w = s o dhat, I = h . w
+  if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 as float pairs itself
+    sp.w = nullptr;
+    sp.w2out = rp.w2;
+    sp.s32 = m.s32;
+    XB_CUDA(sweep(3));
+    sp.w = (float*)h->dhat.p;
+    sp.w2out = nullptr;
+  } else {
+    XB_CUDA(sweep(3));                   // x0 = solve32(b)
+    XB_CUDA(launch_update(rp, 1, st));   // w = s o dhat, I = h . w
+  }
   sp.V = nullptr;
   sp.rhs = (const float*)h->rhat.p;
   sp.accumulate = 1;

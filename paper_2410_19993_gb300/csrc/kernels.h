@@ -95,6 +95,10 @@ struct SweepParams {
   float* max_rel;      // atomic max of |dI| / |I| (accumulate mode), or nullptr
   unsigned* status;
   const int* skip = nullptr;  // if set and nonzero at launch, the kernel does nothing
+  // tensor-core sweep only: write the refinement state w2 = (s32 o w, 0) as float pairs
+  // ([N][Mp][Bpad]) instead of w, so that the first update pass is not needed
+  float2* w2out = nullptr;
+  const float* s32 = nullptr;  // [N][Mp]
 };
 
 template <typename T>
@@ -102,7 +106,7 @@ cudaError_t launch_sweep(const SweepParams<T>& p, cudaStream_t st);
 template <typename T>
 int sweep_panel_width(int Mp, int B, int nsm);
 
-// ---- tensor-core (tcgen05, 3xTF32) FP32 sweeps: panels of 64 vectors, Mp <= 256 -------------
+// ---- tensor-core (tcgen05, three-term BF16) FP32 sweeps: panels of 64 vectors, Mp <= 256 -----
 bool sweep_tc_supported(int Mp);
 int sweep_tc_rows(int Mp);  // rows of the tiled factor (128 or 256)
 constexpr int kSweepTcPanel = 64;

@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
                             : 0.0f;
       const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
+      const float sj = (real && p.w2out) ? p.s32[(size_t)j * Mp + i] : 0.0f;
       // one thread polls the accumulator barrier; the others wait on the named hardware barrier so
       // that no shared-memory polling competes with the tensor core's operand reads
       bool okd = true;
@@ -448,6 +449,10 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
             for (int n = 0; n < 32; n += 4)
               *reinterpret_cast<float4*>(p.w + o + n) =
                   make_float4(a[blk][n], a[blk][n + 1], a[blk][n + 2], a[blk][n + 3]);
+          if (p.w2out && real)  // refinement state (s o w, 0) as float pairs
+#pragma unroll
+            for (int n = 0; n < 32; n += 2)
+              *reinterpret_cast<float4*>(p.w2out + o + n) = make_float4(sj * a[blk][n], 0.0f, sj * a[blk][n + 1], 0.0f);
 #pragma unroll
           for (int n = 0; n < 32; ++n) a[blk][n] *= hj;
           dots[blk] = transpose_sum32(a[blk], lane);
