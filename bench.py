@@ -283,22 +283,26 @@ def run_xbar(args):
     peaks = pipe_peaks(mp.get("sm_max_mhz", 2070.0))
     achieved = work / (ms_launch / 1e3) / 1e12
     if dom == "sweep" and M <= 256:
-        # tensor-core sweep (tcgen05 kind::f16 with BF16 operands, six split products per algorithmic
-        # multiply-add); timed inside a seconds-long step, so the sustained BF16 figure
+        # tensor-core sweep (tcgen05 kind::f16 with BF16 operands: six split products per algorithmic
+        # multiply-add in the initial solve, three in the corrections); timed inside a seconds-long
+        # step, so the sustained BF16 figure
         bf16 = mp.get("bf16_tflops_sustained", mp.get("bf16_tflops", 1704.4))
         bound, peak, note = "tensor", bf16, ("BF16 dense, measured sustained cuBLAS figure (of measured); achieved "
-                                            "counts algorithmic flops only, the kernel issues six BF16 products "
-                                            "(three-term split) per multiply-add")
+                                            "counts algorithmic flops only, averaged over the solve's sweep launches "
+                                            "(the initial one issues six BF16 products per multiply-add, the "
+                                            "corrections three)")
     elif dom in ("sweep", "factor", "update"):
         bound, peak, note = "alu", peaks["fp32_tflops"], "FP32 FMA pipe, 152 SM x 128 lanes x 2 x max SM clock"
     else:
         bound, peak, note = "alu", peaks["fp64_tflops"], "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock"
     traffic, traffic_note = None, None
     if dom == "sweep" and (M, N) == (256, 256) and bound == "tensor":
-        # ncu DRAM read + write of one sweep_tc_kernel launch at B = 2048 (2.280 GB), scaled by
-        # the vectors of this launch: the kernel's streams are per vector
-        traffic = 2.280e9 * B / 2048
-        traffic_note = "ncu dram__bytes_read+write at B=2048 scaled by B (profiles/sweep_tc_xbar256_B2048.md)"
+        # ncu DRAM read + write per sweep_tc_kernel launch at B = 2048, averaged over the solve's
+        # launches (2.263 GB initial, 2.212 GB per correction), scaled by the vectors of this launch:
+        # the kernel's streams are per vector
+        traffic = 2.229e9 * B / 2048
+        traffic_note = ("ncu dram__bytes_read+write at B=2048, mean of the solve's three sweep launches, scaled by B "
+                        "(profiles/sweep_tc_xbar256_B2048.md)")
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note, "peak_note": note,
                 "work_per_launch": work, "ms_per_launch": ms_launch}
