@@ -135,6 +135,24 @@ def test_linearity_and_kirchhoff_on_gpu():
 
 
 # ---------------------------------------------------------------------------------------------
+# long chains with resistive wires: the FP32 factor is least accurate here and the rounding of the
+# two-term BF16 correction sweeps accumulates over 2N - 1 dependent steps; the refinement must
+# still meet the bar (certified by the size of its corrections) in the usual number of passes.
+# (128, 200) runs the one-half (Mt = 128) tensor-core kernels.
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.slow
+@pytest.mark.parametrize("M,N,r_wire", [(256, 256, 2.5), (256, 256, 10.0), (128, 200, 10.0)])
+def test_mixed_resistive_wires_long_chains(M, N, r_wire):
+    R = (1.0, r_wire, r_wire, 10.0)
+    G, V = case(M, N, 200, None, seed=7)
+    Geff = oracle_transfer(M, N, R, seed=7)
+    out = _solve_gpu(G, R, V, "fp32_ir")
+    err = rel_err(out["I"], V @ Geff)
+    assert err <= MIXED_BAR, err
+    assert 1 <= out["info"]["iters"] <= 4
+
+
+# ---------------------------------------------------------------------------------------------
 # full 256 x 256, 8192-vector workload: all currents against the oracle's transfer matrix,
 # a sample of vectors against direct oracle substitution (including node voltages)
 # ---------------------------------------------------------------------------------------------
