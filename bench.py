@@ -342,6 +342,115 @@ def run_xbar(args):
     d.close()
 
 
+def run_transfer(args):
+    """Currents-only transfer-matrix mode on the 256 x 256, 8192-vector inputs: one step is
+    set_conductances + factor(FP32_IR) + xbar_transfer_matrix (M unit solves) + xbar_solve_transfer
+    (I = V G_eff in FP64).  A different path from the substitutions, reported on its own line."""
+    import torch
+
+    from paper_2410_19993_gb300 import inputs, xbar
+
+    d = Dist()
+    rank, world, local = d.rank, d.world, d.local
+    torch.cuda.set_device(local)
+    w = inputs.WORKLOADS["xbar256_mixed"]
+    M, N, B = w.M, w.N, (args.batch or w.B)
+    R = w.circuits[0].as_tuple()
+    G, V = inputs.crossbar(M, N, B, seed=w.seed + rank, g_lo=w.g_lo, g_hi=w.g_hi, v_max=w.v_max)
+    stream = torch.cuda.current_stream()
+    Gd = torch.from_numpy(G).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    I64 = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    xb = xbar.Crossbar.assemble(Gd, *R, stream=stream)
+    info_box = {}
+
+    def step():
+        xb.set_conductances(Gd)
+        xb.factor("fp32_ir")
+        _, info = xb.transfer_matrix(tol=TOL, max_iter=10)
+        info_box.update(info)
+        xb.solve_transfer(Vd, I)
+
+    def timed(fn, K):
+        d.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d.barrier()
+        return e0.elapsed_time(e1) / 1e3
+
+    for _ in range(args.warmup):
+        step()
+    cvd = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    clocks = Clocks(int(cvd[local]) if local < len(cvd) and cvd[local].isdigit() else local)
+    xb.profile_enable(True)
+    clocks.start()
+    t_step = d.max(timed(step, args.steps))
+    clk = clocks.stop()
+    prof = xb.profile_read(reset=True)
+    xb.profile_enable(False)
+    value = d.sum(float(B * args.steps)) / t_step
+    I_t = I.cpu().numpy()
+    # the FP64 product alone (G_eff cached): its own roofline, FP64 pipe
+    t_gemm = d.max(timed(lambda: xb.solve_transfer(Vd, I), 10)) / 10
+    gemm_tflops = 2.0 * B * M * N / t_gemm / 1e12
+    peaks = pipe_peaks(measured_peaks().get("sm_max_mhz", 2070.0))
+
+    # plain FP64 substitution path on the same GPU, and the error against it
+    def step_fp64():
+        xb.set_conductances(Gd)
+        xb.factor("fp64")
+        xb.solve(Vd, I64)
+
+    step_fp64()
+    t64 = d.max(timed(step_fp64, args.fp64_steps))
+    fp64_value = d.sum(float(B * args.fp64_steps)) / t64
+    I_fp64 = I64.cpu().numpy()
+    err_vs_fp64 = float(np.max(np.abs(I_t - I_fp64) / np.maximum(np.abs(I_fp64), 1e-300)))
+    cpu, err_vs_oracle = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, Iref = cpu_baseline(M, N, G, R, V, args.cpu_sample)
+        err_vs_oracle = float(np.max(np.abs(I_t - Iref) / np.abs(Iref)))
+    per_step = {ph: {"launches": v["launches"] / args.steps, "ms": v["ms"] / args.steps}
+                for ph, v in prof.items() if v["launches"]}
+    out = {
+        "metric": "solves/s, currents-only transfer-matrix mode (G_eff from M unit solves + FP64 product) at "
+                  "\u22641e-8 rel. current error",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 product; G_eff from the f32 (bf16x3) + f32-pair refinement solve",
+        "data": "synthetic",
+        "config": {"workload": "xbar256_transfer" + (f"_B{B}" if args.batch else ""), "M": M, "N": N, "B": B,
+                   "R_s": R[0], "R_w": R[1], "R_b": R[2], "R_sense": R[3], "tol": TOL,
+                   "step": "set_conductances + factor(fp32_ir) + transfer_matrix (M unit solves) + FP64 product",
+                   "parallelism": f"replicas{world}"},
+        "fp64_baseline": {"value": fp64_value, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                          "path": "FP64 factor + FP64 substitutions"},
+        "speedup_vs_fp64": value / fp64_value,
+        "rel_err_vs_fp64_gpu": err_vs_fp64,
+        "rel_err_vs_oracle": err_vs_oracle,
+        "refinement_of_unit_solves": {k: info_box.get(k) for k in ("iters", "max_rel_dI", "err_est")},
+        "phases_per_step": per_step,
+        "roofline": {"kernel": "gemm_f64 (I = V G_eff)", "bound": "alu", "achieved": gemm_tflops,
+                     "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": gemm_tflops / peaks["fp64_tflops"],
+                     "traffic": None, "peak_note": "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock",
+                     "ms_per_launch": 1e3 * t_gemm, "work_per_launch": 2.0 * B * M * N},
+        "cpu_baseline": cpu,
+        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    xb.destroy()
+    d.close()
+
+
 def cpu_baseline(M, N, G, R, V, sample):
     """The oracle as it stands on the host cores: one factorization plus `sample` substitutions."""
     import oracle
@@ -614,6 +723,8 @@ def main():
         run_tiles(args)
     elif args.workload == "surrogate128":
         run_surrogate(args)
+    elif args.workload == "xbar256_transfer":
+        run_transfer(args)
     else:
         run_xbar(args)
 

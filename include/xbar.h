@@ -200,6 +200,40 @@ xbar_status xbar_profile_read(xbar_t h, xbar_profile* out, int reset);
  */
 xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I);
 
+/*
+ * Transfer-matrix (currents-only) mode.  The nodal system of Sec. II (Eqs. 1-7)
+ * is linear in the word-line source voltages, so the bit-line currents of any
+ * input vector are I = V G_eff with the M x N transfer matrix
+ * G_eff[i][j] = dI_j / dV_i (the currents for a unit voltage on word line i
+ * alone).  This mode answers currents only (no node voltages) and is a
+ * different path from the substitutions: it is reported separately.
+ *
+ * xbar_transfer_matrix -- G_eff of the handle's current factorization, from M
+ * unit-input solves through xbar_solve (same precision, tol and max_iter
+ * meaning; for XBAR_FP32_IR each entry then carries the certified relative
+ * error of a current).  It is kept in the handle until the next xbar_factor or
+ * xbar_set_conductances; a call while it is valid does no solves.
+ *   Geff  optional M x N row-major copy (device or host memory; NULL: none).
+ *   info  optional: the unit solves' refinement summary (zeros when cached).
+ * Synchronises the handle's stream.  Errors: XBAR_EINVAL (NULL handle),
+ * XBAR_ESTATE (not factored), the errors of xbar_solve, XBAR_ECUDA.
+ *
+ * xbar_solve_transfer -- I = V G_eff for B input vectors: one FP64 matrix
+ * product (2 M N flops per vector), accumulated over the word lines in order.
+ * For non-negative V every term is non-negative (the inverse of the nodal
+ * matrix is entrywise positive), so the relative error of each current is at
+ * most that of the G_eff entries plus FP64 rounding; for signed inputs the
+ * bound is relative to sum_i |V_i| G_eff[i][j].
+ *   B  number of input vectors, >= 0.   V  B x M (device or host memory).
+ *   I  B x N output (device or host memory).
+ * Asynchronous on the handle's stream for device pointers; host pointers are
+ * staged and the call synchronises.  Errors: XBAR_EINVAL (NULL handle, V or I;
+ * B < 0), XBAR_ESTATE (no valid G_eff: call xbar_transfer_matrix after the
+ * last xbar_factor), XBAR_ECUDA.
+ */
+xbar_status xbar_transfer_matrix(xbar_t h, double tol, int max_iter, double* Geff, xbar_solve_info* info);
+xbar_status xbar_solve_transfer(xbar_t h, int B, const double* V, double* I);
+
 /* ---------------------------------------------------------------------------------------------
  * Batches of tiles: many crossbars of uneven sizes, such as the tiles a network layer is mapped
  * onto or the parts of a large crossbar split as in Sec. III-C ("Partitioning"), factored and

@@ -241,6 +241,7 @@ static xbar_status do_factor(xbar_t h, bool equilibrate, bool upload) {
 
 xbar_status xbar::factor_handle(xbar_s* h, xbar_precision p, bool upload_params) {
   h->factored = 0;
+  h->geff_valid = 0;
   if (!h->assembled) {  // the elimination data of the current conductances
     PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
     XB_CUDA(launch_assemble(h->m, h->st));
@@ -662,6 +663,7 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
     Gd = (const double*)h->sV.p;
   }
   h->factored = 0;
+  h->geff_valid = 0;
   h->assembled = 0;
   {
     PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
@@ -711,6 +713,66 @@ cudaError_t noalloc_scratch(int dev, void** out) {
   return cudaSuccess;
 }
 }  // namespace
+
+// ---- transfer-matrix mode (currents only) ------------------------------------------------------
+extern "C" xbar_status xbar_transfer_matrix(xbar_t h, double tol, int max_iter, double* Geff, xbar_solve_info* info) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (info) memset(info, 0, sizeof(*info));
+  if (!h->factored) return fail(XBAR_ESTATE, "xbar_transfer_matrix called before xbar_factor");
+  XB_CUDA(cudaSetDevice(h->dev));
+  const int M = h->m.M, N = h->m.N;
+  const size_t n = (size_t)M * N;
+  if (!h->geff_valid) {  // M unit-input solves of the current factorization: row i of I is G_eff[i][:]
+    XB_CUDA(ensure(h->A, h->geff, n * 8));
+    XB_CUDA(ensure(h->A, h->eye, (size_t)M * M * 8));
+    XB_CUDA(launch_eye((double*)h->eye.p, M, h->st));
+    xbar_solve_info si;
+    const xbar_status s = xbar_solve(h, M, (const double*)h->eye.p, (double*)h->geff.p, nullptr, nullptr, tol,
+                                     max_iter, &si);
+    if (info) *info = si;
+    if (s != XBAR_OK) return s;  // message set by xbar_solve
+    h->geff_valid = 1;
+  }
+  if (Geff) {
+    XB_CUDA(cudaMemcpyAsync(Geff, h->geff.p, n * 8, cudaMemcpyDefault, h->st));
+    if (!is_device_ptr(Geff)) XB_CUDA(cudaStreamSynchronize(h->st));
+  }
+  return check_status(h);
+}
+
+extern "C" xbar_status xbar_solve_transfer(xbar_t h, int B, const double* V, double* I) {
+  if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (!h->factored || !h->geff_valid)
+    return fail(XBAR_ESTATE, "xbar_solve_transfer needs xbar_transfer_matrix after the last xbar_factor");
+  if (B < 0) return fail(XBAR_EINVAL, "B=%d < 0", B);
+  if (B == 0) return XBAR_OK;
+  if (!V || !I) return fail(XBAR_EINVAL, "V and I must not be NULL");
+  XB_CUDA(cudaSetDevice(h->dev));
+  const int M = h->m.M, N = h->m.N;
+  cudaStream_t st = h->st;
+  const bool vdev = is_device_ptr(V), idev = is_device_ptr(I);
+  const size_t nVB = (size_t)B * M, nIB = (size_t)B * N;
+  const double* dV = V;
+  double* dI = I;
+  if (!vdev) {
+    XB_CUDA(ensure(h->A, h->sV, nVB * 8));
+    XB_CUDA(cudaMemcpyAsync(h->sV.p, V, nVB * 8, cudaMemcpyHostToDevice, st));
+    dV = (const double*)h->sV.p;
+  }
+  if (!idev) {
+    XB_CUDA(ensure(h->A, h->sI, nIB * 8));
+    dI = (double*)h->sI.p;
+  }
+  {
+    PhaseScope ps(h, XBAR_PHASE_SWEEP);  // the product replaces the substitutions
+    XB_CUDA(launch_gemm_f64(dV, (const double*)h->geff.p, dI, B, M, N, st));
+  }
+  if (!idev) {  // host output: synchronise (and report device status), as xbar_solve does
+    XB_CUDA(cudaMemcpyAsync(I, dI, nIB * 8, cudaMemcpyDeviceToHost, st));
+    return check_status(h);
+  }
+  return XBAR_OK;  // asynchronous on the handle's stream
+}
 
 extern "C" xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I) {
   if (!h) return fail(XBAR_EINVAL, "handle is NULL");

@@ -102,6 +102,9 @@ struct xbar_s {
   xbar::Buf z, dhat, rhat, w64, phi, maxrel, rmax, irstate;
   // staging for host pointers
   xbar::Buf sV, sI, svWL, svBL;
+  // transfer-matrix mode: G_eff of the current factorization (valid until the next factor)
+  xbar::Buf geff, eye;
+  int geff_valid = 0;
   // profiling: events recorded around launches, resolved in xbar_profile_read
   int prof_on = 0;
   std::vector<cudaEvent_t> ev_pool;

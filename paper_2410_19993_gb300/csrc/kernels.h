@@ -116,6 +116,11 @@ cudaError_t launch_sweep_tc_tile(const float* X, void* Xt, int Mp, int N, cudaSt
 // terms = leading BF16 terms of the split used (1..3): 3 gives FP32-level accuracy
 cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, int terms, cudaStream_t st);
 
+// ---- transfer-matrix mode (transfer.cu) -------------------------------------------------------
+cudaError_t launch_eye(double* E, int M, cudaStream_t st);  // E = I (M x M, FP64)
+// C[R x N] = A[R x K] . B[K x N], FP64, row-major
+cudaError_t launch_gemm_f64(const double* A, const double* B, double* C, int R, int K, int N, cudaStream_t st);
+
 // ---- BF16 tensor-core GEMM (gemm_bf16.cu): C[m][n] = sum_k A(m,k) B(n,k) ---------------------
 enum { GEMM_EPI_STORE = 0, GEMM_EPI_BIAS_RELU = 1, GEMM_EPI_MASK = 2 };
 struct GemmBf16Params {

@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
     lib.xbar_sync.argtypes = [_vp]
     lib.xbar_set_conductances.argtypes = [_vp, _vp]
     lib.xbar_solve_noalloc.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    lib.xbar_transfer_matrix.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _vp, ctypes.POINTER(SolveInfo)]
+    lib.xbar_solve_transfer.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     lib.xbar_set_option.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     lib.xbar_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(TileDesc), _vp, ctypes.POINTER(_vp)]
     lib.xbar_batch_run.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp),
@@ -107,6 +109,7 @@ def load(build_if_missing: bool = True):
     lib.xbar_version.restype = ctypes.c_char_p
     for f in ("xbar_assemble", "xbar_factor", "xbar_solve", "xbar_sync", "xbar_destroy", "xbar_set_conductances",
               "xbar_profile_enable", "xbar_profile_read", "xbar_solve_noalloc", "xbar_set_option",
+              "xbar_transfer_matrix", "xbar_solve_transfer",
               "xbar_batch_create", "xbar_batch_run", "xbar_batch_autotune", "xbar_batch_tile",
               "xbar_batch_destroy", "xbar_surrogate_create", "xbar_surrogate_params", "xbar_surrogate_grad",
               "xbar_surrogate_scaling",
@@ -179,6 +182,22 @@ class Crossbar:
     def solve_noalloc(self, V, I, raise_on_error=True):
         """xbar_solve_noalloc: FP64 substitution with library-internal fixed scratch (device V, I only)."""
         st = load().xbar_solve_noalloc(self.handle, int(V.shape[0]), _ptr(V), _ptr(I))
+        if raise_on_error:
+            _check(st)
+        return st
+
+    def transfer_matrix(self, tol=1e-9, max_iter=10, Geff=None, raise_on_error=True):
+        """xbar_transfer_matrix: G_eff (M x N) of the current factorization from M unit solves (cached
+        until the next factor); optionally copied into Geff. Returns (status, info dict)."""
+        info = SolveInfo()
+        st = load().xbar_transfer_matrix(self.handle, tol, max_iter, _ptr(Geff), ctypes.byref(info))
+        if raise_on_error:
+            _check(st)
+        return st, info.as_dict()
+
+    def solve_transfer(self, V, I, raise_on_error=True):
+        """xbar_solve_transfer: I = V G_eff (currents only), one FP64 product."""
+        st = load().xbar_solve_transfer(self.handle, int(V.shape[0]), _ptr(V), _ptr(I))
         if raise_on_error:
             _check(st)
         return st
