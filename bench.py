@@ -451,6 +451,96 @@ def run_transfer(args):
     d.close()
 
 
+def run_paper_experiments(args):
+    """The paper's timing experiments (Sec. III) re-run on this implementation: simulation time of
+    m x n crossbars for m, n in {2, ..., 256} (one input vector), a 256 x 256 crossbar partitioned
+    into t x t tiles (all tiles in one CUDA-graph launch of the tile batch), and the decomposition /
+    solve split for batches of 1, 2, 10, 100 and 1000.  Parasitic resistors 5 Ohm each (source and
+    sense resistors equal to the wire segments), random conductances and voltages as elsewhere.
+    Each time is the wall time of the user-visible calls with the stream synchronised, mean of 10
+    runs; the FP64 path is the paper's method (LU in FP64), the mixed path is given beside it."""
+    import torch
+
+    from paper_2410_19993_gb300 import inputs, xbar
+
+    torch.cuda.set_device(0)
+    R = (5.0, 5.0, 5.0, 5.0)
+    runs = 10
+    sizes = [2, 4, 8, 16, 32, 64, 128, 256]
+
+    def wall(fn, n=runs):
+        fn()  # warm-up (allocations, lazy setup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0) / n
+
+    # (a) simulation time per crossbar size, one input vector
+    size_sweep = []
+    for m in sizes:
+        for n in sizes:
+            G, V = inputs.crossbar(m, n, 1, seed=0)
+            Gd, Vd = torch.from_numpy(G).cuda(), torch.from_numpy(V).cuda()
+            I = torch.zeros((1, n), dtype=torch.float64, device="cuda")
+            xb = xbar.Crossbar.assemble(Gd, *R)
+            row = {"m": m, "n": n}
+            for prec in ("fp64", "fp32_ir"):
+                def sim():
+                    xb.set_conductances(Gd)
+                    xb.factor(prec)
+                    xb.solve(Vd, I, tol=TOL, max_iter=10)
+                row[prec + "_ms"] = wall(sim)
+            xb.destroy()
+            size_sweep.append(row)
+
+    # (b) 256 x 256 partitioned into t x t tiles, one input vector
+    M = N = 256
+    G, V = inputs.crossbar(M, N, 1, seed=0)
+    partition = []
+    for t in (256, 128, 64, 32, 16):
+        tiles, Vs, Is = [], [], []
+        for r0 in range(0, M, t):
+            for c0 in range(0, N, t):
+                tiles.append((torch.from_numpy(np.ascontiguousarray(G[r0:r0 + t, c0:c0 + t])).cuda(), *R))
+                Vs.append(torch.from_numpy(np.ascontiguousarray(V[:, r0:r0 + t])).cuda())
+                Is.append(torch.zeros((1, t), dtype=torch.float64, device="cuda"))
+        b = xbar.Batch(tiles)
+        row = {"tile": t, "tiles": len(tiles)}
+        for prec in ("fp64", "fp32_ir"):
+            row[prec + "_ms"] = wall(lambda: b.run(prec, Vs, Is, tol=TOL, max_iter=6))
+        b.destroy()
+        partition.append(row)
+
+    # (c) decomposition / solve split per batch size
+    split = []
+    for m in (32, 128, 256):
+        for B in (1, 2, 10, 100, 1000):
+            G, V = inputs.crossbar(m, m, B, seed=0)
+            Gd, Vd = torch.from_numpy(G).cuda(), torch.from_numpy(V).cuda()
+            I = torch.zeros((B, m), dtype=torch.float64, device="cuda")
+            xb = xbar.Crossbar.assemble(Gd, *R)
+            row = {"m": m, "n": m, "B": B}
+            for prec in ("fp64", "fp32_ir"):
+                def dec():
+                    xb.set_conductances(Gd)
+                    xb.factor(prec)
+                t_dec = wall(dec)
+                t_sol = wall(lambda: xb.solve(Vd, I, tol=TOL, max_iter=10))
+                row[prec] = {"decompose_ms": t_dec, "solve_ms": t_sol, "solve_share": t_sol / (t_dec + t_sol),
+                             "per_sample_ms": (t_dec + t_sol) / B}
+            xb.destroy()
+            split.append(row)
+
+    out = {"metric": "simulation time of the paper's experiments (Sec. III), this implementation", "value": None,
+           "unit": "ms", "n_gpus": 1, "data": "synthetic", "higher_is_better": False,
+           "config": {"workload": "paper_experiments", "R_s": R[0], "R_w": R[1], "R_b": R[2], "R_sense": R[3],
+                      "runs": runs, "tol": TOL},
+           "size_sweep": size_sweep, "partition_256": partition, "batch_split": split}
+    print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(M, N, G, R, V, sample):
     """The oracle as it stands on the host cores: one factorization plus `sample` substitutions."""
     import oracle
@@ -725,6 +815,8 @@ def main():
         run_surrogate(args)
     elif args.workload == "xbar256_transfer":
         run_transfer(args)
+    elif args.workload == "paper_experiments":
+        run_paper_experiments(args)
     else:
         run_xbar(args)
 

@@ -14,7 +14,15 @@
 // Data movement: X_j is streamed through shared memory in chunks of KC rows by the bulk-copy
 // (TMA) engine, double-buffered and completed on mbarriers with bounded waits; the running
 // vector of the panel stays in shared memory; each thread accumulates a TR x TC register tile.
+//
+// Two tilings.  Wide panels use 8 x 4 (FP64) or 8 x 8 (FP32) register tiles.  A panel of a small
+// batch would then be one or two warps, each warp's FMAs issued on a single SM sub-partition (for
+// FP64, a quarter of the SM's DFMA rate), with most of a TC-wide tile spent on padding columns.
+// So when the wide tiling gives fewer than four warps the kernel runs with 2 x 1 tiles instead and
+// the panel is exactly ceil(B / SMs) vectors wide: a batch of one is Mp/2 threads.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -28,9 +36,21 @@ struct SweepCfg<float> { static constexpr int TR = 8, TC = 8, KC = 32; };
 template <>
 struct SweepCfg<double> { static constexpr int TR = 8, TC = 4, KC = 16; };
 
+// the narrow tiling (all precisions)
+constexpr int kNarrowTR = 2, kNarrowTC = 1;
+constexpr int kMinWarps = 4;
+// threads per block: at most 512 for the wide tilings (128 registers each), 1024 for the narrow one
+template <int TR, int TC>
+constexpr int sweep_max_threads() { return TR * TC >= 8 ? 512 : 1024; }
+
 template <typename T>
-static size_t sweep_smem_bytes(int Mp, int Bp, int KC) {
-  constexpr int TR = SweepCfg<T>::TR;
+static bool sweep_is_narrow(int Mp, int Bp) {
+  constexpr int TR = SweepCfg<T>::TR, TC = SweepCfg<T>::TC;
+  return Bp % TC != 0 || (Mp / TR) * (Bp / TC) < 32 * kMinWarps;
+}
+
+template <typename T>
+static size_t sweep_smem_bytes(int Mp, int Bp, int KC, int TR) {
   const int nrg = Mp / TR;
   size_t n = (size_t)Mp * Bp + 2 * (size_t)KC * Mp + (size_t)nrg * Bp;
   return n * sizeof(T) + 64;
@@ -49,30 +69,40 @@ template <typename T>
 int sweep_panel_width(int Mp, int B, int nsm) {
   constexpr int TR = SweepCfg<T>::TR, TC = SweepCfg<T>::TC;
   const int nrg = Mp / TR;
-  int bp = (B + nsm - 1) / nsm;
-  bp = ((bp + TC - 1) / TC) * TC;
-  if (bp < TC) bp = TC;
-  // threads <= 1024 and shared memory <= 200 KB
-  while (bp > TC && (nrg * (bp / TC) > 1024 ||
-                     sweep_smem_bytes<T>(Mp, bp, sweep_kc<T>(Mp)) > 200 * 1024))
-    bp -= TC;
-  return bp;
+  const int kc = sweep_kc<T>(Mp);
+  const int per_sm = std::max(1, (B + nsm - 1) / nsm);
+  int bp = ((per_sm + TC - 1) / TC) * TC;
+  constexpr int wide_max = sweep_max_threads<TR, TC>(), narrow_max = sweep_max_threads<kNarrowTR, kNarrowTC>();
+  // threads within the launch bound and shared memory <= 200 KB
+  while (bp > TC && (nrg * (bp / TC) > wide_max || sweep_smem_bytes<T>(Mp, bp, kc, TR) > 200 * 1024)) bp -= TC;
+  if (!sweep_is_narrow<T>(Mp, bp)) return bp;
+  // fewer than four warps: narrow tiles, no padding columns.  Every width up to bp is narrow too
+  // ((Mp/TR)*(Bp/TC) only grows with Bp), so launch_sweep picks the same tiling from (Mp, Bp).
+  int nb = std::min(per_sm, bp);
+  while (nb > 1 && ((Mp / kNarrowTR) * nb > narrow_max || sweep_smem_bytes<T>(Mp, nb, kc, kNarrowTR) > 200 * 1024))
+    --nb;
+  return nb;
 }
 
-// n consecutive elements from 16-byte aligned shared memory with 16-byte loads
+// n consecutive elements from shared memory: 16-byte loads when the run is a multiple of 16 bytes
+// (and then 16-byte aligned), element loads otherwise
 template <typename T, int n>
 __device__ __forceinline__ void load_vec(T (&r)[n], const T* p) {
-  static_assert((n * sizeof(T)) % 16 == 0, "vector width");
-  constexpr int per = 16 / sizeof(T);
+  if constexpr ((n * sizeof(T)) % 16 == 0) {
+    constexpr int per = 16 / sizeof(T);
 #pragma unroll
-  for (int q = 0; q < n / per; ++q) {
-    const float4 v = *reinterpret_cast<const float4*>(p + q * per);
-    memcpy(&r[q * per], &v, 16);
+    for (int q = 0; q < n / per; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(p + q * per);
+      memcpy(&r[q * per], &v, 16);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < n; ++q) r[q] = p[q];
   }
 }
 
 template <typename T, int TR, int TC>
-__global__ void sweep_kernel(SweepParams<T> p, int KC) {
+__global__ void __launch_bounds__(sweep_max_threads<TR, TC>()) sweep_kernel(SweepParams<T> p, int KC) {
   const int Mp = p.Mp, N = p.N, Bp = p.Bp, Bpad = p.Bpad;
   const int nrg = Mp / TR, ncg = Bp / TC;
   const int tid = threadIdx.x;
@@ -197,12 +227,28 @@ __global__ void sweep_kernel(SweepParams<T> p, int KC) {
 #pragma unroll
         for (int b = 0; b < TC; ++b) part[b] = fma(hv, acc[a][b], part[b]);
       }
+      // when whole warps hold whole column groups (ncg divides 32) the lanes of one column group
+      // are summed by shuffles first and one partial per warp goes through shared memory
+      const bool wred = (blockDim.x & 31) == 0 && (32 % ncg) == 0;
+      int nq = nrg;
+      if (wred) {
+        const int lane = tid & 31;
 #pragma unroll
-      for (int b = 0; b < TC; ++b) red[(size_t)rg * Bp + c0 + b] = part[b];
+        for (int b = 0; b < TC; ++b)
+          for (int o = 16; o >= ncg; o >>= 1) part[b] += __shfl_xor_sync(0xffffffffu, part[b], o);
+        if (lane < ncg) {
+#pragma unroll
+          for (int b = 0; b < TC; ++b) red[(size_t)(tid >> 5) * Bp + c0 + b] = part[b];
+        }
+        nq = blockDim.x >> 5;
+      } else {
+#pragma unroll
+        for (int b = 0; b < TC; ++b) red[(size_t)rg * Bp + c0 + b] = part[b];
+      }
       __syncthreads();
       for (int t = tid; t < Bp; t += blockDim.x) {
         T sum = 0;
-        for (int q = 0; q < nrg; ++q) sum += red[(size_t)q * Bp + t];
+        for (int q = 0; q < nq; ++q) sum += red[(size_t)q * Bp + t];
         const int b = b0 + t;
         if (b < p.B) {
           double* Ip = p.I + (size_t)b * N + j;
@@ -246,22 +292,28 @@ __global__ void sweep_kernel(SweepParams<T> p, int KC) {
   }
 }
 
-template <typename T>
-cudaError_t launch_sweep(const SweepParams<T>& p, cudaStream_t st) {
-  constexpr int TR = SweepCfg<T>::TR, TC = SweepCfg<T>::TC;
-  const int KC = sweep_kc<T>(p.Mp);
+template <typename T, int TR, int TC>
+static cudaError_t launch_tiled(const SweepParams<T>& p, int KC, cudaStream_t st) {
   if (p.Mp % TR || p.Bp % TC || p.Mp % KC) return cudaErrorInvalidValue;
-  const int nrg = p.Mp / TR, ncg = p.Bp / TC;
-  const int threads = nrg * ncg;
-  if (threads > 1024) return cudaErrorInvalidConfiguration;
+  const int threads = (p.Mp / TR) * (p.Bp / TC);
+  if (threads > sweep_max_threads<TR, TC>()) return cudaErrorInvalidConfiguration;
   const int blocks = (p.B + p.Bp - 1) / p.Bp;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = sweep_smem_bytes<T>(p.Mp, p.Bp, KC);
+  if ((long long)blocks * p.Bp > p.Bpad) return cudaErrorInvalidValue;
+  const size_t smem = sweep_smem_bytes<T>(p.Mp, p.Bp, KC, TR);
   cudaError_t err = cudaFuncSetAttribute(sweep_kernel<T, TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
   sweep_kernel<T, TR, TC><<<blocks, threads, smem, st>>>(p, KC);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep(const SweepParams<T>& p, cudaStream_t st) {
+  if (p.Mp <= 0 || p.Bp <= 0) return cudaErrorInvalidValue;
+  const int KC = sweep_kc<T>(p.Mp);
+  if (sweep_is_narrow<T>(p.Mp, p.Bp)) return launch_tiled<T, kNarrowTR, kNarrowTC>(p, KC, st);
+  return launch_tiled<T, SweepCfg<T>::TR, SweepCfg<T>::TC>(p, KC, st);
 }
 
 template int sweep_panel_width<float>(int, int, int);
