@@ -216,18 +216,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     for (int r = tid; r < R; r += kThreads) p.sig[(size_t)(j & 1) * Mp + r0 + r] = sg[(j & 1) * R + r];
 
-    // (2) X^_{j-1} own rows to the output
-    if (j > 0) {
-      float* Xo = p.X + (size_t)(j - 1) * Mp * Mp + (size_t)r0 * Mp;
-      for (int t = tid; t < R * Mp; t += kThreads) Xo[t] = rows[t];
-    }
-
-    // (3) Z^_j own rows: off-diagonal, then the subtraction-free diagonal
+    // (2) + (3) Z^_j own rows (off-diagonal, then the subtraction-free diagonal) in place of
+    // X^_{j-1}, whose own rows go to the output on the way: each element of `rows` is read, stored
+    // to X and overwritten by the same thread, so no thread can overwrite an element of X^_{j-1}
+    // before it has been stored
+    float* Xo = j > 0 ? p.X + (size_t)(j - 1) * Mp * Mp + (size_t)r0 * Mp : nullptr;
     for (int t = tid * 2; t < R * Mp; t += kThreads * 2) {
       const int r = t / Mp, k = t - r * Mp, i = r0 + r;
       const double2 c2 = *reinterpret_cast<const double2*>(Cj + t);
       const float si = sv[i], ei = ev[i];
       const float x0 = j > 0 ? rows[t] : 0.0f, x1 = j > 0 ? rows[t + 1] : 0.0f;  // X^_{j-1}
+      if (j > 0) *reinterpret_cast<float2*>(Xo + t) = make_float2(x0, x1);
       float v0 = 0.0f, v1 = 0.0f;
       if (i < M) {
         if (k < M && k != i) v0 = si * sv[k] * (float)c2.x - ei * ev[k] * x0;
