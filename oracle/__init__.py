@@ -91,7 +91,8 @@ def assemble_band(M, N, G, Rs, Rw, Rb, Rsense):
     ab = np.zeros((2 * M * N, 2 * p + 1), dtype=np.float64)
     rc = _load().xref_assemble_band(M, N, _ptr(G), Rs, Rw, Rb, Rsense, _ptr(ab))
     if rc != 0:
-        raise ValueError("xref_assemble_band rejected its arguments")
+        raise ValueError(f"xref_assemble_band failed (rc={rc}): -1 invalid arguments, "
+                         "-2 a node index outside the matrix or its band")
     return ab, p
 
 

@@ -59,9 +59,22 @@ static size_t idx_bl(int N, int i, int j) { return idx_wl(N, i, j) + 1; }
 
 int xref_half_bandwidth(int M, int N) { (void)M; return 2 * N; }
 
-/* band storage: row r holds entries c in [r-p, r+p] at ab[r*(2p+1) + (c-r+p)] */
-static void band_add(double* ab, int p, size_t r, size_t c, double v) {
-  ab[r * (size_t)(2 * p + 1) + (size_t)((long long)c - (long long)r + p)] += v;
+/* band storage: row r holds entries c in [r-p, r+p] at a[r*(2p+1) + (c-r+p)] of a k x k matrix.
+ * An entry outside the matrix or outside the band is not stored and marks the assembly as
+ * failed: a wrong node index must fail loudly instead of writing past the array. */
+typedef struct {
+  double* a;
+  size_t k;
+  int bad;
+} Band;
+
+static void band_add(Band* ab, int p, size_t r, size_t c, double v) {
+  const long long d = (long long)c - (long long)r;
+  if (r >= ab->k || c >= ab->k || d < -p || d > p) {
+    ab->bad = 1;
+    return;
+  }
+  ab->a[r * (size_t)(2 * p + 1) + (size_t)(d + p)] += v;
 }
 
 /*
@@ -69,16 +82,18 @@ static void band_add(double* ab, int p, size_t r, size_t c, double v) {
  * G is M x N row-major (G[i*N+j] is the conductance of device D(i,j)).
  * Each row is the KCL equation of its node written as
  *   (sum of conductances at the node) * V_node - sum_k g_k * V_neighbour_k = injected current.
- * Returns 0, or -1 on invalid arguments.
+ * Returns 0, -1 on invalid arguments, or -2 if a node index fell outside the matrix or band.
  */
 int xref_assemble_band(int M, int N, const double* G, double Rs, double Rw, double Rb,
-                       double Rsense, double* ab) {
-  if (M < 1 || N < 1 || !G || !ab) return -1;
+                       double Rsense, double* abuf) {
+  if (M < 1 || N < 1 || !G || !abuf) return -1;
   if (!(Rs > 0) || !(Rw > 0) || !(Rb > 0) || !(Rsense > 0)) return -1;
   const double gs = 1.0 / Rs, gw = 1.0 / Rw, gb = 1.0 / Rb, go = 1.0 / Rsense;
   const int p = 2 * N;
   const size_t k = 2 * (size_t)M * (size_t)N;
-  memset(ab, 0, k * (size_t)(2 * p + 1) * sizeof(double));
+  memset(abuf, 0, k * (size_t)(2 * p + 1) * sizeof(double));
+  Band band = {abuf, k, 0};
+  Band* ab = &band;
   for (int i = 0; i < M; ++i) {
     for (int j = 0; j < N; ++j) {
       const double g = G[(size_t)i * N + j];
@@ -111,7 +126,7 @@ int xref_assemble_band(int M, int N, const double* G, double Rs, double Rw, doub
       }
     }
   }
-  return 0;
+  return band.bad ? -2 : 0;
 }
 
 /*
