@@ -202,7 +202,7 @@ def run_xbar(args):
     Is = [torch.zeros((B, N), dtype=torch.float64, device="cuda") for _ in range(2)]
     I64s = [torch.zeros((B, N), dtype=torch.float64, device="cuda") for _ in range(2)]
     info_box = {}
-    pipe = {"k": 0, "prec": None}
+    pipe = {"k": 0, "prec": None, "solved": set()}
 
     def prime(prec):
         """Factor map 0 before a run of pipelined steps (outside any timed region)."""
@@ -218,6 +218,7 @@ def run_xbar(args):
         nxt.set_conductances(Gd)  # map k+1: set, assembled and factored on its own stream ...
         nxt.factor(pipe["prec"])
         _, info = cur.solve(V_in, outs[k % 2], **solve_kwargs)  # ... beside map k's solve
+        pipe["solved"].add((id(outs), k % 2))
         pipe["k"] = k + 1
         return info
 
@@ -281,7 +282,9 @@ def run_xbar(args):
     total_solves = d.sum(float(B * args.steps))
     value = total_solves / t_mixed
     I_mixed = Is[(args.steps - 1) % 2].cpu().numpy()
-    assert np.array_equal(Is[0].cpu().numpy(), Is[1].cpu().numpy()), "the two maps' solves differ"
+    for b_ in (0, 1):  # both maps hold the same conductances: equal currents, bit for bit
+        if (id(Is), b_) in pipe["solved"]:
+            assert np.array_equal(Is[b_].cpu().numpy(), I_mixed), "the two maps' solves differ"
 
     # the same steps one map at a time (no overlap between the factor and the solve)
     step_mixed_sequential()
