@@ -33,6 +33,11 @@
  *     volts); I is B x N (amperes); node voltages are B x M x N.
  *   - Every call returns an xbar_status; none exits or throws.  On failure
  *     xbar_last_error() returns a message for the calling thread.
+ *   - Handles share no state: different handles may be used at the same time
+ *     from different host threads, and their work may overlap on the GPU when
+ *     they run on different streams (for example, factoring the next
+ *     conductance map while another handle solves).  One handle must not be
+ *     used from two threads at once.
  *   - Errors detected on the device (a bounded wait that timed out, a
  *     non-finite value) are recorded in a device status word and reported by
  *     the next call that synchronises (xbar_solve always does when it
