@@ -96,6 +96,10 @@ struct xbar_s {
   xbar_opts opt;
   // factor
   xbar::Buf X, fsig, fpbuf, fbar, fparams;
+  // host copy of the parameter block last uploaded to `fparams` (skip identical uploads)
+  unsigned char fparams_host[sizeof(xbar::FactorParams<double>)] = {};
+  size_t fparams_bytes = 0;
+  const void* fparams_dev = nullptr;
   xbar::Buf Xt;    // tensor-core tiled TF32 hi/lo copy of the FP32 factor
   int tc_ready = 0;
   // solve workspace
