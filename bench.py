@@ -64,14 +64,21 @@ def dist_env():
 
 
 class Dist:
-    def __init__(self):
+    """Replicas only: a barrier and max/sum reductions of timing scalars across ranks (NCCL on the
+    GPUs; gloo with CPU tensors where there is no GPU, as in the multi-process CPU tests)."""
+
+    def __init__(self, backend="nccl"):
         import torch
         self.rank, self.world, self.local = dist_env()
         self.torch = torch
         self.pg = None
+        self.dev = "cuda" if backend == "nccl" else "cpu"
         if self.world > 1:
             import torch.distributed as dist
-            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            else:
+                dist.init_process_group(backend)
             self.pg = dist
 
     def barrier(self):
@@ -81,14 +88,14 @@ class Dist:
     def max(self, x: float) -> float:
         if not self.pg:
             return x
-        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
+        t = self.torch.tensor([x], dtype=self.torch.float64, device=self.dev)
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
         return float(t.item())
 
     def sum(self, x: float) -> float:
         if not self.pg:
             return x
-        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
+        t = self.torch.tensor([x], dtype=self.torch.float64, device=self.dev)
         self.pg.all_reduce(t)
         return float(t.item())
 
