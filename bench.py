@@ -27,6 +27,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -115,7 +116,7 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"xbar_clocks_{os.getpid()}_gpu{gpu_index}.csv")
 
     def start(self):
         try:
@@ -690,7 +691,7 @@ def run_tiles(args):
     b = xbar.Batch([(t.G, *t.circuit.as_tuple()) for t in tiles])
     Bs = [t.V.shape[0] for t in tiles]
     t0 = time.perf_counter()
-    b.autotune("fp32_ir", Bs, os.path.join(ROOT, "gpurun_out", "autotune_tiles.json"))
+    b.autotune("fp32_ir", Bs, os.path.join(tempfile.gettempdir(), "xbar_autotune_tiles.json"))
     t_tune = time.perf_counter() - t0
     total = float(sum(Bs))
 
