@@ -46,3 +46,36 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.xbar_factor(None, 0) == xbar.XBAR_EINVAL
     assert lib.xbar_solve(None, 1, None, None, None, None, 1e-8, 4, None) == xbar.XBAR_EINVAL
     assert lib.xbar_destroy(None) == xbar.XBAR_OK
+
+
+def test_null_handles_are_rejected_without_gpu():
+    """Every entry point taking a handle rejects NULL with XBAR_EINVAL before any CUDA call."""
+    import numpy as np
+    lib = xbar.load()
+    V = np.zeros((2, 3))
+    I = np.zeros((2, 3))
+    G = np.zeros(9)
+    assert lib.xbar_set_conductances(None, G.ctypes.data) == xbar.XBAR_EINVAL
+    assert lib.xbar_set_option(None, 0, 1) == xbar.XBAR_EINVAL
+    assert lib.xbar_sync(None) == xbar.XBAR_EINVAL
+    assert lib.xbar_profile_enable(None, 1) == xbar.XBAR_EINVAL
+    assert lib.xbar_profile_read(None, None, 0) == xbar.XBAR_EINVAL
+    assert lib.xbar_transfer_matrix(None, 1e-9, 10, None, None) == xbar.XBAR_EINVAL
+    assert lib.xbar_solve_transfer(None, 2, V.ctypes.data, I.ctypes.data) == xbar.XBAR_EINVAL
+    assert lib.xbar_solve_noalloc(None, 2, V.ctypes.data, I.ctypes.data) == xbar.XBAR_EINVAL
+    assert b"NULL" in lib.xbar_last_error()
+
+
+def test_binding_marshals_only_contiguous_float64():
+    """The binding passes pointers of contiguous float64 arrays and refuses anything else."""
+    import numpy as np
+    import pytest
+    a = np.zeros((3, 4))
+    assert xbar._ptr(a) == a.ctypes.data
+    assert xbar._ptr(None) is None
+    with pytest.raises(TypeError):
+        xbar._ptr(np.zeros((3, 4), dtype=np.float32))
+    with pytest.raises(TypeError):
+        xbar._ptr(a[:, ::2])  # not contiguous
+    with pytest.raises(TypeError):
+        xbar._ptr([1.0, 2.0])
