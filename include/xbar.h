@@ -143,19 +143,37 @@ xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, double* vWL,
 /* Kernel-variant options of a handle (value -1 = automatic choice). */
 typedef enum {
   XBAR_OPT_SWEEP_KERNEL = 0,  /* FP32 substitutions: 0 = CUDA-core kernel, 1 = tensor-core kernel */
-  XBAR_OPT_FACTOR_KERNEL = 1  /* FP32 factor: 0 = cooperative-group kernel, 1 = cluster kernel */
+  XBAR_OPT_FACTOR_KERNEL = 1, /* FP32 factor: 0 = cooperative-group kernel, 1 = cluster kernel */
+  XBAR_OPT_ALGORITHM = 2,     /* factor + substitution: 0 = block Thomas over the columns (N
+                                 dependent block steps), 1 = block cyclic reduction over the
+                                 columns (ceil(log2 N) levels of independent dense block products;
+                                 M <= 256).  Takes effect at the next xbar_factor. */
+  XBAR_OPT_CR_PRODUCTS = 3,   /* cyclic reduction in XBAR_FP32_IR: 0 = products on the CUDA
+                                 cores, 1 = on the tensor cores (three-term BF16 split; M >= 128) */
+  XBAR_OPT_WAIT_LIMIT_NS = 4  /* limit of every bounded device-side wait of this handle's
+                                 kernels, in ns (value > 0); -1 or 0 restores the default of 2 s.
+                                 A wait that runs out makes its kernel record a timeout and
+                                 return; the next call that reads the handle's device status
+                                 returns XBAR_ETIMEOUT and the results of that work are invalid.
+                                 Synchronises the handle's stream. */
 } xbar_option;
 
-/* Select a kernel variant for later xbar_factor / xbar_solve calls; a variant that does not
- * support the handle's size falls back to the other.  Errors: XBAR_EINVAL. */
+/* Select a kernel variant for later xbar_factor / xbar_solve calls (value -1, 0 or 1; a
+ * variant that does not support the handle's size falls back to the other), or set the wait
+ * limit (XBAR_OPT_WAIT_LIMIT_NS).  Errors: XBAR_EINVAL, XBAR_ECUDA. */
 xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value);
 
 /*
  * xbar_set_conductances -- load a new conductance map G into the handle (same
- * M, N and resistances; host or device pointer, validated as in xbar_assemble)
- * without reallocating.  The handle becomes unfactored; as after xbar_assemble,
- * the column elimination data are formed by the next xbar_factor.
- * Errors: XBAR_EINVAL (NULL handle/G, negative or non-finite G), XBAR_ECUDA.
+ * M, N and resistances; host or device pointer) without reallocating.  The
+ * handle becomes unfactored; as after xbar_assemble, the column elimination
+ * data are formed by the next xbar_factor.  A host G is validated before the
+ * call returns.  A device G is read and validated on the device, asynchronously
+ * on the handle's stream (the call does not wait for that stream): a negative or
+ * non-finite entry is reported as XBAR_EINVAL by the next call that reads the
+ * handle's device status (xbar_sync, an XBAR_FP32_IR xbar_solve, a solve with
+ * host buffers), and results computed from such a map are meaningless.
+ * Errors: XBAR_EINVAL (NULL handle/G, negative or non-finite host G), XBAR_ECUDA.
  */
 xbar_status xbar_set_conductances(xbar_t h, const double* G);
 
@@ -198,10 +216,13 @@ xbar_status xbar_profile_read(xbar_t h, xbar_profile* out, int reset);
  * larger requests fail with XBAR_EINVAL and a message giving the sizes.
  * Nothing is allocated or freed.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array, so calls whose work overlaps
- * on the GPU race on it.  Work is asynchronous on the handle's stream.
- * Errors: XBAR_ESTATE (not factored with XBAR_FP64), XBAR_EINVAL (NULL or host
- * pointers, B < 0, scratch too large), XBAR_ECUDA.
+ * any stream capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that replaces the device's primary context)
+ * the entry point must not be used again in that process.  All calls share the
+ * array, so calls whose work overlaps on the GPU race on it.  Work is
+ * asynchronous on the handle's stream.
+ * Errors: XBAR_ESTATE (not factored with XBAR_FP64 by block Thomas), XBAR_EINVAL
+ * (NULL or host pointers, B < 0, scratch too large), XBAR_ECUDA.
  */
 xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I);
 

@@ -1,5 +1,6 @@
 // api.cu -- host implementation of the libxbar C ABI (include/xbar.h).
 #include <math.h>
+#include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -51,7 +52,24 @@ xbar_status xbar::set_error(xbar_status st, const char* fmt, ...) {
     }                                                                                      \
   } while (0)
 
-static const char* kVersion = "libxbar 0.1 (sm_103a)";
+static const char* kVersion = "libxbar 0.2 (sm_103a)";
+
+bool xbar::alloc_injected_failure() {
+  static std::mutex mu;
+  static std::string armed;
+  static long long count = 0;
+  const char* v = getenv("XBAR_FAIL_ALLOC_AFTER");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!v || !*v) {
+    armed.clear();
+    return false;
+  }
+  if (armed != v) {  // a new value re-arms the counter
+    armed = v;
+    count = 0;
+  }
+  return count++ >= atoll(v);
+}
 
 extern "C" const char* xbar_version(void) { return kVersion; }
 extern "C" const char* xbar_last_error(void) { return g_last_error.c_str(); }
@@ -63,6 +81,8 @@ static xbar_status check_status(xbar_t h) {
   if (s) {
     XB_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
     if (s & XBAR_DEV_TIMEOUT) return fail(XBAR_ETIMEOUT, "a bounded device wait expired (status 0x%x)", s);
+    if (s & XBAR_DEV_BADINPUT)
+      return fail(XBAR_EINVAL, "a conductance passed in device memory was negative or non-finite (status 0x%x)", s);
     if (s & XBAR_DEV_BADLAUNCH) return fail(XBAR_ECUDA, "kernel launch shape inconsistent (status 0x%x)", s);
     if (s & XBAR_DEV_NONFINITE) return fail(XBAR_ECUDA, "non-finite value produced (status 0x%x)", s);
   }
@@ -143,22 +163,31 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   XB_ALLOC(m.h2, nv * 8);
   XB_ALLOC(m.tha2, nv * 8);
   XB_ALLOC(m.thc2, nv * 8);
-  XB_ALLOC(h->status, sizeof(unsigned));
+  XB_ALLOC(h->status, sizeof(DevStatus));
   double* Gd = nullptr;
   XB_ALLOC(Gd, (size_t)M * N * 8);
 #undef XB_ALLOC
-  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
+  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->st);  // no bits, default wait limit
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(Gd, Gh.data(), (size_t)M * N * 8, cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess) {
     PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
-    e = launch_store_g(m, Gd, h->st);
+    e = launch_store_g(m, Gd, nullptr, h->st);  // validated on the host above
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cleanup(fail(XBAR_ECUDA, "assembly: %s", cudaGetErrorString(e)));
   h->A.release(Gd);
   *out = h;
   return XBAR_OK;
+}
+
+// kernel launches of one cyclic-reduction substitution (for the per-phase launch counts)
+static int cr_sweep_launches(const xbar_s* h, int B, bool initial) {
+  (void)B;
+  const int L = (int)(h->prec == XBAR_FP64 ? h->cr64.lv.size() : h->cr32.lv.size());
+  // right-hand side (or pad clear), last block, back levels, currents; forward levels in
+  // correction mode (level 0: two launches)
+  return 3 + L + (initial ? 0 : L + 1);
 }
 
 // BF16 terms of the tensor-core sweep for refinement correction `it` (0-based).  A correction
@@ -186,6 +215,35 @@ bool xbar::use_cluster_factor(const xbar_s* h) {
   if (e && strcmp(e, "group") == 0) return false;
   if (e && strcmp(e, "cluster") == 0) return true;
   return h->opt.factor != 0;
+}
+
+// Block cyclic reduction when the handle's option (or XBAR_ALGO=cr|thomas) asks for it and the
+// block fits (Mp <= 256); block Thomas otherwise.
+bool xbar::use_cr(const xbar_s* h) {
+  if (!cr_supported(h->m.Mp, h->m.N)) return false;
+  const char* e = getenv("XBAR_ALGO");
+  if (e && strcmp(e, "thomas") == 0) return false;
+  if (e && strcmp(e, "cr") == 0) return true;
+  return h->opt.algo == 1;
+}
+
+// FP32 cyclic-reduction products on the tensor cores when the blocks are at least 128 rows
+static bool use_cr_tensor(const xbar_s* h) {
+  if (h->m.Mp < 128) return false;
+  const char* e = getenv("XBAR_CR_PRODUCTS");
+  if (e && strcmp(e, "simt") == 0) return false;
+  if (e && strcmp(e, "tc") == 0) return true;
+  return h->opt.cr_tensor != 0;
+}
+
+template <typename T>
+static xbar_status do_factor_cr(xbar_t h, bool equilibrate) {
+  xbar::CrPlan<T>& pl = *reinterpret_cast<xbar::CrPlan<T>*>(sizeof(T) == 4 ? (void*)&h->cr32 : (void*)&h->cr64);
+  const bool tensor = sizeof(T) == 4 && use_cr_tensor(h);
+  XB_CUDA(xbar::cr_prepare<T>(h, pl, tensor));  // level plan and buffers (once per shape)
+  PhaseScope ps(h, XBAR_PHASE_FACTOR, (int)pl.ops.size());
+  XB_CUDA(xbar::cr_factor<T>(h, pl, tensor, equilibrate));
+  return XBAR_OK;
 }
 
 template <typename T>
@@ -259,9 +317,13 @@ xbar_status xbar::factor_handle(xbar_s* h, xbar_precision p, bool upload_params)
     XB_CUDA(launch_assemble(h->m, h->st));
     h->assembled = 1;
   }
-  xbar_status s = (p == XBAR_FP64) ? do_factor<double>(h, false, upload_params)
-                                   : do_factor<float>(h, true, upload_params);
+  const bool cr = use_cr(h);
+  h->tc_ready = 0;
+  xbar_status s;
+  if (cr) s = (p == XBAR_FP64) ? do_factor_cr<double>(h, false) : do_factor_cr<float>(h, true);
+  else s = (p == XBAR_FP64) ? do_factor<double>(h, false, upload_params) : do_factor<float>(h, true, upload_params);
   if (s != XBAR_OK) return s;
+  h->cr_active = cr ? 1 : 0;
   h->prec = p;
   h->factored = 1;
   return XBAR_OK;
@@ -276,10 +338,23 @@ extern "C" xbar_status xbar_factor(xbar_t h, xbar_precision p) {
 
 extern "C" xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value) {
   if (!h) return fail(XBAR_EINVAL, "handle is NULL");
+  if (opt == XBAR_OPT_WAIT_LIMIT_NS) {
+    if (value < -1) return fail(XBAR_EINVAL, "wait limit %d ns < -1", value);
+    XB_CUDA(cudaSetDevice(h->dev));
+    h->wait_ns = value > 0 ? (unsigned long long)value : 0ull;  // 0: the default
+    // pageable source: the copy is staged before the call returns, and later kernels of the
+    // stream see the new limit
+    XB_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(h->status) + offsetof(DevStatus, wait_ns), &h->wait_ns,
+                            sizeof(h->wait_ns), cudaMemcpyHostToDevice, h->st));
+    XB_CUDA(cudaStreamSynchronize(h->st));
+    return XBAR_OK;
+  }
   if (value < -1 || value > 1) return fail(XBAR_EINVAL, "option value %d outside [-1, 1]", value);
   switch (opt) {
     case XBAR_OPT_SWEEP_KERNEL: h->opt.sweep = value; break;
     case XBAR_OPT_FACTOR_KERNEL: h->opt.factor = value; break;
+    case XBAR_OPT_ALGORITHM: h->opt.algo = value; break;
+    case XBAR_OPT_CR_PRODUCTS: h->opt.cr_tensor = value; break;
     default: return fail(XBAR_EINVAL, "unknown option %d", (int)opt);
   }
   return XBAR_OK;
@@ -334,9 +409,11 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     dvBL = (double*)h->svBL.p;
   }
 
-  const bool tc = mixed && h->tc_ready;
-  const int Bp = tc ? kSweepTcPanel
-                    : (mixed ? sweep_panel_width<float>(Mp, B, h->nsm) : sweep_panel_width<double>(Mp, B, h->nsm));
+  const bool cr = h->cr_active != 0;
+  const bool tc = mixed && h->tc_ready && !cr;
+  const int Bp = cr ? kCrPanel
+                    : tc ? kSweepTcPanel
+                         : (mixed ? sweep_panel_width<float>(Mp, B, h->nsm) : sweep_panel_width<double>(Mp, B, h->nsm));
   const int nblk = (B + Bp - 1) / Bp;
   const int Bpad = nblk * Bp;
   const size_t nst = (size_t)N * Mp * Bpad;
@@ -365,10 +442,8 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
   bool converged = true;
   if (!mixed) {
     XB_CUDA(ensure(h->A, h->z, nst * 8));
-    if (want_v) {
-      XB_CUDA(ensure(h->A, h->w64, nst * 8));
-      XB_CUDA(ensure(h->A, h->phi, nst * 8));
-    }
+    if (want_v || cr) XB_CUDA(ensure(h->A, h->w64, nst * 8));
+    if (want_v) XB_CUDA(ensure(h->A, h->phi, nst * 8));
     SweepParams<double> sp;
     sp.M = M;
     sp.Mp = Mp;
@@ -388,7 +463,21 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     sp.accumulate = 0;
     sp.max_rel = nullptr;
     sp.status = h->status;
-    {
+    if (cr) {
+      PhaseScope ps(h, XBAR_PHASE_SWEEP, cr_sweep_launches(h, B, true));
+      CrSweepArgs<double> ca;
+      memset(&ca, 0, sizeof(ca));
+      ca.B = B;
+      ca.Bpad = Bpad;
+      ca.V = dV;
+      ca.src = m.src_pl;
+      ca.r = (double*)h->z.p;
+      ca.x = (double*)h->w64.p;
+      ca.e = m.e_pl;
+      ca.hs = m.h;
+      ca.I = dI;
+      XB_CUDA(cr_sweep<double>(h, h->cr64, ca));
+    } else {
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
       XB_CUDA(launch_sweep<double>(sp, st));
     }
@@ -432,6 +521,26 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     sp.accumulate = 0;
     sp.max_rel = nullptr;
     sp.status = h->status;
+    // FP32 substitution of the factor's algorithm (CUDA-core block-Thomas sweep, or cyclic
+    // reduction with the right-hand side in z (initial) or rhat (corrections), both overwritten)
+    auto sweep32 = [&](const SweepParams<float>& q) -> cudaError_t {
+      if (!cr) return launch_sweep<float>(q, st);
+      CrSweepArgs<float> ca;
+      memset(&ca, 0, sizeof(ca));
+      ca.B = B;
+      ca.Bpad = Bpad;
+      ca.V = q.V;
+      ca.src = m.src32;
+      ca.r = q.V ? (float*)h->z.p : (float*)h->rhat.p;
+      ca.x = q.w;
+      ca.e = m.e32;
+      ca.hs = m.hs32;
+      ca.I = q.I;
+      ca.accumulate = q.accumulate;
+      ca.max_rel = q.max_rel;
+      ca.tensor = use_cr_tensor(h) && Bpad >= 128;  // wide batches: products on the tensor cores
+      return cr_sweep<float>(h, h->cr32, ca);
+    };
     if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 as float pairs itself
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
       sp.w = nullptr;
@@ -442,8 +551,8 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       sp.w2out = nullptr;
     } else {
       {
-        PhaseScope ps(h, XBAR_PHASE_SWEEP);
-        XB_CUDA(launch_sweep<float>(sp, st));  // x0 = solve32(b)
+        PhaseScope ps(h, XBAR_PHASE_SWEEP, cr ? cr_sweep_launches(h, B, true) : 1);
+        XB_CUDA(sweep32(sp));                   // x0 = solve32(b)
       }
       PhaseScope ps(h, XBAR_PHASE_UPDATE);
       XB_CUDA(launch_update(rp, 1, st));        // w = s o dhat, I = h . w
@@ -463,9 +572,9 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       sp.accumulate = 1;
       sp.max_rel = (float*)h->maxrel.p;
       {
-        PhaseScope ps(h, XBAR_PHASE_SWEEP);     // dhat = solve32(rhat), I += dI
+        PhaseScope ps(h, XBAR_PHASE_SWEEP, cr ? cr_sweep_launches(h, B, false) : 1);  // dhat = solve32(rhat), I += dI
         if (tc) XB_CUDA(launch_sweep_tc(sp, h->Xt.p, correction_terms(it), st));
-        else XB_CUDA(launch_sweep<float>(sp, st));
+        else XB_CUDA(sweep32(sp));
       }
       w_current = false;
       ++iters;
@@ -537,6 +646,8 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   MapDev& m = h->m;
   const int M = m.M, Mp = m.Mp, N = m.N;
   cudaStream_t st = h->st;
+  if (h->cr_active)
+    return fail(XBAR_ESTATE, "device-driven solves (tile batches) need a block-Thomas factorization");
   const bool mixed = h->prec == XBAR_FP32_IR;
   const bool tc = mixed && h->tc_ready;
   const int Bp = tc ? kSweepTcPanel
@@ -658,28 +769,22 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
   MapDev& m = h->m;
   const size_t n = (size_t)m.M * m.N;
   const bool gdev = is_device_ptr(G);
-  // validation needs the values on the host
-  std::vector<double> Gh(n);
-  if (gdev) {
-    XB_CUDA(cudaMemcpyAsync(Gh.data(), G, n * 8, cudaMemcpyDeviceToHost, h->st));
-    XB_CUDA(cudaStreamSynchronize(h->st));
-  } else {
-    memcpy(Gh.data(), G, n * 8);
-  }
-  for (size_t k = 0; k < n; ++k)
-    if (!(Gh[k] >= 0.0) || !isfinite(Gh[k])) return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, Gh[k]);
-  XB_CUDA(ensure(h->A, h->sV, std::max(h->sV.bytes, n * 8)));
   const double* Gd = G;
-  if (!gdev) {
-    XB_CUDA(cudaMemcpyAsync(h->sV.p, Gh.data(), n * 8, cudaMemcpyHostToDevice, h->st));
+  if (!gdev) {  // host map: validated here, then staged
+    for (size_t k = 0; k < n; ++k)
+      if (!(G[k] >= 0.0) || !isfinite(G[k])) return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, G[k]);
+    XB_CUDA(ensure(h->A, h->sV, std::max(h->sV.bytes, n * 8)));
+    XB_CUDA(cudaMemcpyAsync(h->sV.p, G, n * 8, cudaMemcpyHostToDevice, h->st));
     Gd = (const double*)h->sV.p;
   }
   h->factored = 0;
   h->geff_valid = 0;
   h->assembled = 0;
   {
+    // a device map is validated by the transposing kernel itself (status word, reported by the
+    // next call that reads it), so the host does not wait for the stream here
     PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
-    XB_CUDA(launch_store_g(m, Gd, h->st));
+    XB_CUDA(launch_store_g(m, Gd, gdev ? h->status : nullptr, h->st));
   }
   if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
   return XBAR_OK;
@@ -788,8 +893,8 @@ extern "C" xbar_status xbar_solve_transfer(xbar_t h, int B, const double* V, dou
 
 extern "C" xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I) {
   if (!h) return fail(XBAR_EINVAL, "handle is NULL");
-  if (!h->factored || h->prec != XBAR_FP64)
-    return fail(XBAR_ESTATE, "xbar_solve_noalloc needs a handle factored with XBAR_FP64");
+  if (!h->factored || h->prec != XBAR_FP64 || h->cr_active)
+    return fail(XBAR_ESTATE, "xbar_solve_noalloc needs a handle factored with XBAR_FP64 by block Thomas");
   if (B < 0) return fail(XBAR_EINVAL, "B=%d < 0", B);
   if (B == 0) return XBAR_OK;
   if (!V || !I) return fail(XBAR_EINVAL, "V and I must not be NULL");

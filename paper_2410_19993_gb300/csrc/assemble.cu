@@ -19,12 +19,15 @@
 
 namespace xbar {
 
-// Gc[j][i] = G[i][j] (row-major M x N input), zero in the padding rows i >= M.
-__global__ void asm_gc_kernel(MapDev m, const double* __restrict__ G) {
+// Gc[j][i] = G[i][j] (row-major M x N input), zero in the padding rows i >= M.  With `status`
+// set, every entry is also checked (finite and >= 0) and XBAR_DEV_BADINPUT recorded otherwise.
+__global__ void asm_gc_kernel(MapDev m, const double* __restrict__ G, unsigned* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= m.Mp || j >= m.N) return;
-  m.Gc[(size_t)j * m.Mp + i] = i < m.M ? G[(size_t)i * m.N + j] : 0.0;
+  const double g = i < m.M ? G[(size_t)i * m.N + j] : 0.0;
+  if (status && !(g >= 0.0 && g <= 1.79e308)) set_status(status, XBAR_DEV_BADINPUT);
+  m.Gc[(size_t)j * m.Mp + i] = g;
 }
 
 // One thread per bit line j: the chain recurrences of T_j (sequential in i), from Gc.
@@ -151,9 +154,9 @@ __global__ void asm_coff_kernel(MapDev m) {
   for (int k = M; k < Mp; ++k) C[(size_t)k * Mp + i] = 0.0;
 }
 
-cudaError_t launch_store_g(const MapDev& m, const double* G_dev, cudaStream_t st) {
+cudaError_t launch_store_g(const MapDev& m, const double* G_dev, unsigned* status, cudaStream_t st) {
   dim3 g((m.Mp + 127) / 128, m.N);
-  asm_gc_kernel<<<g, 128, 0, st>>>(m, G_dev);
+  asm_gc_kernel<<<g, 128, 0, st>>>(m, G_dev, status);
   return cudaGetLastError();
 }
 

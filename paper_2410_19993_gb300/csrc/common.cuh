@@ -15,13 +15,29 @@ namespace xbar {
 enum : unsigned {
   XBAR_DEV_TIMEOUT = 1u,    // a bounded wait expired
   XBAR_DEV_NONFINITE = 2u,  // a NaN/Inf was produced where none may appear
-  XBAR_DEV_BADLAUNCH = 4u   // a kernel found its launch shape inconsistent with its arguments
+  XBAR_DEV_BADLAUNCH = 4u,  // a kernel found its launch shape inconsistent with its arguments
+  XBAR_DEV_BADINPUT = 8u    // an input checked on the device was invalid (negative or non-finite G)
 };
 
 // default limit of every device-side wait: 2 s
 #ifndef XBAR_WAIT_LIMIT_NS
 #define XBAR_WAIT_LIMIT_NS 2000000000ull
 #endif
+
+// Device status block of a handle (16 bytes, the `status` pointer the kernels receive points at
+// its first word): status bits, padding, then the wait limit in nanoseconds (0 = the default).
+struct DevStatus {
+  unsigned bits;
+  unsigned pad;
+  unsigned long long wait_ns;
+};
+
+// limit of the bounded waits of a kernel launched with this status block
+__device__ __forceinline__ uint64_t wait_limit(const unsigned* status) {
+  if (!status) return XBAR_WAIT_LIMIT_NS;
+  const uint64_t v = *reinterpret_cast<const volatile unsigned long long*>(status + 2);
+  return v ? v : XBAR_WAIT_LIMIT_NS;
+}
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;

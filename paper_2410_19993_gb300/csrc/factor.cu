@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kFactorThreads)
   __shared__ unsigned flag;
   __shared__ T rinv_s;
 
-  const uint64_t limit = XBAR_WAIT_LIMIT_NS;
+  const uint64_t limit = wait_limit(status);
   const T gw = (T)p.gw;
   const int npanel = Mp / PB;
 

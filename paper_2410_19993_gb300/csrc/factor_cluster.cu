@@ -64,7 +64,7 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, unsigned par
   const uint64_t t0 = globaltimer_ns();
   unsigned k = 0;
   while (!done()) {
-    if ((++k & 255u) == 0 && globaltimer_ns() - t0 > XBAR_WAIT_LIMIT_NS) {
+    if ((++k & 255u) == 0 && globaltimer_ns() - t0 > wait_limit(status)) {
       set_status(status, XBAR_DEV_TIMEOUT);
       return false;
     }
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int M = p.M, Mp = p.Mp, N = p.N;
   const int r0 = (int)g * R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t wlim = wait_limit(status);
   constexpr int nwarps = kThreads / 32;
 
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const double* hj = stj + (size_t)R * Mp + 3 * Mp;          // own rows: hj[r] is h_j of row r0 + r
     if (tid == 0) {
       if (j + 1 < N) stage_inputs(j + 1);
-      if (!failed && !mbar_wait_bounded(&pbar[j & 1], (unsigned)((j >> 1) & 1), status, XBAR_WAIT_LIMIT_NS))
+      if (!failed && !mbar_wait_bounded(&pbar[j & 1], (unsigned)((j >> 1) & 1), status, wlim))
         failed = 1;
     }
     __syncthreads();

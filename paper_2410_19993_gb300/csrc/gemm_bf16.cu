@@ -93,6 +93,7 @@ __device__ __forceinline__ void stage(unsigned char* dst, const __nv_bfloat16* P
 __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Params p) {
   using namespace g16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
   const long m0 = (long)blockIdx.x * kBM, n0 = (long)blockIdx.y * kBN;
   const int nks = p.K / kBK;                                  // K chunks of the whole product
   const int per = (nks + (int)gridDim.z - 1) / (int)gridDim.z;  // chunks of this split
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Par
     unsigned char* At = tiles + (size_t)buf * 2 * kTileBytes;
     unsigned char* Bt = At + kTileBytes;
     if (it >= 2)  // the MMAs that read this buffer two chunks ago are complete
-      ok = mbar_spin_bounded(&bar[buf], (unsigned)(((it - 2) >> 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 20);
+      ok = mbar_spin_bounded(&bar[buf], (unsigned)(((it - 2) >> 1) & 1), p.status, wlim, 20);
     if (__syncthreads_or(!ok)) break;
     stage(At, p.A, p.sAm, p.sAk, m0, (long)kc * kBK, tid);
     stage(Bt, p.B, p.sBn, p.sBk, n0, (long)kc * kBK, tid);
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(g16::kThreads, 1) gemm_bf16_kernel(GemmBf16Par
   }
   if (ok && kc1 > kc0) {
     const int last = kc1 - kc0 - 1;
-    ok = mbar_spin_bounded(&bar[last & 1], (unsigned)((last >> 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 20);
+    ok = mbar_spin_bounded(&bar[last & 1], (unsigned)((last >> 1) & 1), p.status, wlim, 20);
   }
   ok = !__syncthreads_or(!ok);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

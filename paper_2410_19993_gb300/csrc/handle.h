@@ -11,11 +11,18 @@
 
 namespace xbar {
 // device allocation owned by a handle; freed in reverse order on destroy
+// Allocation-failure injection for tests (host side only): with XBAR_FAIL_ALLOC_AFTER=n in the
+// environment, the allocations through any DevArena after the first n (counted from the moment
+// the variable took its current value) fail with cudaErrorMemoryAllocation without calling
+// cudaMalloc.  Unset, it costs one getenv per allocation.
+bool alloc_injected_failure();
+
 struct DevArena {
   std::vector<void*> ptrs;
   cudaError_t alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (alloc_injected_failure()) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
@@ -63,6 +70,12 @@ inline cudaError_t ensure(DevArena& A, Buf& b, size_t bytes) {
 
 inline int round_up(int a, int m) { return ((a + m - 1) / m) * m; }
 
+}  // namespace xbar
+
+#include "cr.h"
+
+namespace xbar {
+
 
 // per-handle refinement state on the device (graph-driven solves)
 struct IrState {
@@ -81,6 +94,8 @@ struct IrState {
 struct xbar_opts {
   int sweep = -1;   // 0 = CUDA-core FP32 sweep, 1 = tensor-core sweep
   int factor = -1;  // 0 = cooperative-group factor, 1 = cluster factor
+  int algo = -1;    // 0 = block Thomas, 1 = block cyclic reduction
+  int cr_tensor = -1;  // cyclic reduction, FP32 products: 0 = CUDA cores, 1 = tensor cores
 };
 
 struct xbar_s {
@@ -92,7 +107,8 @@ struct xbar_s {
   int factored = 0;
   xbar_precision prec = XBAR_FP64;
   xbar::DevArena A;
-  unsigned* status = nullptr;
+  unsigned* status = nullptr;      // device status block (xbar::DevStatus)
+  unsigned long long wait_ns = 0;  // limit of the device waits, 0 = the default (host copy)
   xbar_opts opt;
   // factor
   xbar::Buf X, fsig, fpbuf, fbar, fparams;
@@ -106,6 +122,10 @@ struct xbar_s {
   xbar::Buf z, dhat, rhat, w64, phi, maxrel, rmax, irstate;
   // staging for host pointers
   xbar::Buf sV, sI, svWL, svBL;
+  // block cyclic reduction (cr.cu): plans of both precisions; cr_active = factored by it
+  xbar::CrPlan<float> cr32;
+  xbar::CrPlan<double> cr64;
+  int cr_active = 0;
   // transfer-matrix mode: G_eff of the current factorization (valid until the next factor)
   xbar::Buf geff, eye;
   int geff_valid = 0;
@@ -154,6 +174,10 @@ xbar_status set_error(xbar_status s, const char* fmt, ...);
 // kernel-variant selection (environment XBAR_SWEEP=simt|tc, XBAR_FACTOR=group|cluster override)
 bool use_tc_sweep(const xbar_s* h);
 bool use_cluster_factor(const xbar_s* h);
+// block cyclic reduction (handle option XBAR_OPT_ALGORITHM, environment XBAR_ALGO=cr|thomas)
+bool use_cr(const xbar_s* h);
+// input vectors per panel of the cyclic-reduction substitution (Bpad = B rounded up to it)
+constexpr int kCrPanel = 16;
 
 // factor a handle (FP64 or equilibrated FP32); upload_params = false reuses the parameter block
 // already on the device (graph capture)

@@ -43,8 +43,9 @@ struct MapDev {
 };
 
 // ---- assembly ---------------------------------------------------------------------------------
-// Gc <- G (transposed to [N][Mp]); the rest of the assembly reads Gc only
-cudaError_t launch_store_g(const MapDev& m, const double* G_dev, cudaStream_t st);
+// Gc <- G (transposed to [N][Mp]); the rest of the assembly reads Gc only.  status != NULL: check
+// G on the device (XBAR_DEV_BADINPUT for a negative or non-finite entry)
+cudaError_t launch_store_g(const MapDev& m, const double* G_dev, unsigned* status, cudaStream_t st);
 cudaError_t launch_assemble(const MapDev& m, cudaStream_t st);
 
 // ---- factor -----------------------------------------------------------------------------------
@@ -163,6 +164,46 @@ struct SurInferParams {
   unsigned* status;
 };
 cudaError_t launch_surrogate_infer(const SurInferParams& p, int nsm, cudaStream_t st);
+
+// ---- batched GEMM job lists (gemm_jobs.cu, gemm_jobs_tc.cu) -----------------------------------
+// One job: C = Cin + alpha * sum_s op(A_s) op(B_s)   (Cin may be NULL: then C = alpha * sum; Cin
+// may equal C).  op(A_s) is m x k_s: ta = 0 reads A_s[i * lda + kk], ta = 1 reads A_s[kk * lda + i];
+// op(B_s) is k_s x n: tb = 0 reads B_s[kk * ldb + j], tb = 1 reads B_s[j * ldb + kk].  All jobs of
+// one launch share m and n; each is cut into row x column tiles of the kernel's tile shape.
+template <typename T>
+struct GemmJob {
+  T* C;
+  const T* Cin;
+  int ldc, ldcin;
+  int nseg;
+  T alpha;
+  const T* A[3];
+  const T* B[3];
+  int lda[3], ldb[3], k[3];
+  int ta[3], tb[3];
+};
+// CUDA cores (FP32 or FP64), 64 x 64 output tiles
+template <typename T>
+cudaError_t launch_gemm_jobs(const GemmJob<T>* jobs_dev, int njobs, int m, int n, unsigned* status, cudaStream_t st);
+// tensor cores (tcgen05, FP32 operands split into three BF16 terms, six products per K step, FP32
+// accumulation in tensor memory), 128 x TN output tiles with TN = 128 or 256, persistent over the
+// SMs.  k_s must be multiples of 16.
+cudaError_t launch_gemm_jobs_tc(const GemmJob<float>* jobs_dev, int njobs, int m, int n, int tn, int nsm,
+                                unsigned* status, cudaStream_t st);
+
+// In-place Gauss-Jordan inversion (no pivoting) of symmetric M-matrices, one block per matrix:
+// dst = src^-1 (n x n, n <= 128; src may equal dst)
+template <typename T>
+struct GjJob {
+  const T* src;
+  T* dst;
+  int lds, ldd;
+};
+template <typename T>
+cudaError_t launch_gj_inverse(const GjJob<T>* jobs_dev, int njobs, int n, unsigned* status, cudaStream_t st);
+
+// ---- block cyclic reduction over the columns (cr.cu) ------------------------------------------
+bool cr_supported(int Mp, int N);
 
 // ---- FP64 refinement kernels and node voltages ------------------------------------------------
 struct ResidParams {

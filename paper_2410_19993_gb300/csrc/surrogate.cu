@@ -680,7 +680,7 @@ extern "C" xbar_status xbar_surrogate_create(int M, int N, double R_s, double R_
   if (s->A.alloc((void**)&s->P, s->np * 4) || s->A.alloc((void**)&s->Gr, s->np * 4) ||
       s->A.alloc((void**)&s->Am, s->np * 4) || s->A.alloc((void**)&s->Av, s->np * 4) ||
       s->A.alloc((void**)&s->W1b, (size_t)kH * s->Fp * 2) || s->A.alloc((void**)&s->W2b, (size_t)kH * kH * 2) ||
-      s->A.alloc((void**)&s->loss, 16) || s->A.alloc((void**)&s->status, 4))
+      s->A.alloc((void**)&s->loss, 16) || s->A.alloc((void**)&s->status, sizeof(DevStatus)))
     return bail(set_error(XBAR_ENOMEM, "surrogate parameters"));
   // He initialisation of the weights (padding columns of W1 stay zero), zero biases, small head
   std::vector<float> h(s->np, 0.0f);
@@ -694,7 +694,7 @@ extern "C" xbar_status xbar_surrogate_create(int M, int N, double R_s, double R_
   h[s->ob3 + 1] = logf(1e-3f);
   if (cudaMemcpy(s->P, h.data(), s->np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(s->Am, 0, s->np * 4) != cudaSuccess || cudaMemset(s->Av, 0, s->np * 4) != cudaSuccess ||
-      cudaMemset(s->status, 0, 4) != cudaSuccess)
+      cudaMemset(s->status, 0, sizeof(DevStatus)) != cudaSuccess)
     return bail(set_error(XBAR_ECUDA, "surrogate initialisation"));
   if (refresh_bf16(s) != XBAR_OK) return bail(XBAR_ECUDA);
   *out = s;

@@ -45,6 +45,7 @@ __device__ __forceinline__ uint32_t b_off(int n, int g) { return (uint32_t)g * k
 __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInferParams p) {
   using namespace si;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
   const long ntiles = (p.rows + kRows - 1) / kRows;
 
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
     // the previous tile's MMAs read the operand buffer: wait for them before regenerating it
     if (issued >= 1)
       ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
-                             XBAR_WAIT_LIMIT_NS, 20);
+                             wlim, 20);
     if (__syncthreads_or(!ok)) break;
     umma::fence_after();
     {  // operand of tile t: thread = row m
@@ -172,13 +173,13 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   }
   if (ok && prev >= 0) {
     ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
-                           XBAR_WAIT_LIMIT_NS, 20);
+                           wlim, 20);
     ok = !__syncthreads_or(!ok);
     umma::fence_after();
     if (ok) epilogue(prev, (issued - 1) & 1);
   }
   if (!ok && issued >= 1)  // the last commit covers every MMA of this block: wait for it (bounded)
-    mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 20);
+    mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status, wlim, 20);
   umma::fence_before();
   __syncthreads();
   if (warp == 0) umma::dealloc(tbase, 2 * kH);

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(sweep_max_threads<TR, TC>()) sweep_kernel(Swee
   const int Mp = p.Mp, N = p.N, Bp = p.Bp, Bpad = p.Bpad;
   const int nrg = Mp / TR, ncg = Bp / TC;
   const int tid = threadIdx.x;
+  const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
   const int rg = tid / ncg, cg = tid - rg * ncg;
   const int i0 = rg * TR, c0 = cg * TC;
   const int b0 = blockIdx.x * Bp;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(sweep_max_threads<TR, TC>()) sweep_kernel(Swee
         bulk_g2s(xs + (size_t)nb * KC * Mp, chunk_src(c + 1), chunk_bytes, &mbar[nb]);
       }
       const bool ok = mbar_wait_bounded(&mbar[c & 1], (unsigned)((c >> 1) & 1), p.status,
-                                        XBAR_WAIT_LIMIT_NS);
+                                        wlim);
       if (__syncthreads_or(!ok)) return;
       const T* xb = xs + (size_t)(c & 1) * KC * Mp;
       const T* vb = vin + (size_t)kc * KC * Bp;

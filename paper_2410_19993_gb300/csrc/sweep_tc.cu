@@ -173,6 +173,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   constexpr int NS = tc_stages(Mt);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b0 = blockIdx.x * BP;
+  const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
+
   const int N = p.N, Mp = p.Mp, Bpad = p.Bpad;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       long long issued = 0;
       int st = 0, use = 0, s = 0, kc = 0;  // stage, uses of this stage so far, step, chunk in step
       for (long long c = 0; c < nchunks; ++c) {
-        if (c >= NS && !mbar_spin_bounded(&empty[st], (unsigned)((use - 1) & 1), p.status, XBAR_WAIT_LIMIT_NS, 0))
+        if (c >= NS && !mbar_spin_bounded(&empty[st], (unsigned)((use - 1) & 1), p.status, wlim, 0))
           break;
         issued = c + 1;
         const int j = s < N ? s : 2 * N - 2 - s;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       }
       // before the block may exit: the last copy into each stage has landed (bounded wait)
       for (long long c = (issued > NS ? issued - NS : 0); c < issued; ++c)
-        mbar_wait_bounded(&full[c % NS], (unsigned)((c / NS) & 1), p.status, XBAR_WAIT_LIMIT_NS);
+        mbar_wait_bounded(&full[c % NS], (unsigned)((c / NS) & 1), p.status, wlim);
     }
     __syncwarp();
   } else if (warp == 9) {
@@ -258,11 +260,11 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_part = part_bytes >> 4;
       uint64_t ast = adesc0;  // descriptor of stage mst
       for (int s = 0; s < nsteps; ++s) {
-        bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, XBAR_WAIT_LIMIT_NS, 0);
+        bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, wlim, 0);
         fence_after();
         uint64_t bdesc = bdesc0;  // advances by one K-step (2 node groups of 128 bytes) per chunk
         for (int kc = 0; kc < cps && ok; ++kc) {
-          if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, XBAR_WAIT_LIMIT_NS, 0)) {
+          if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, wlim, 0)) {
             ok = false;
             break;
           }
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       // one thread polls the accumulator barrier; the others wait on the named hardware barrier so
       // that no shared-memory polling competes with the tensor core's operand reads
       bool okd = true;
-      if (tid == 32) okd = mbar_spin_bounded(dfull, (unsigned)(s & 1), p.status, XBAR_WAIT_LIMIT_NS, 64);
+      if (tid == 32) okd = mbar_spin_bounded(dfull, (unsigned)(s & 1), p.status, wlim, 64);
       if (!okd) atomicExch(fail, 1u);
       if (epi_sync_or(*fail != 0)) break;
       fence_after();

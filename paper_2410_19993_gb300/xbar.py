@@ -51,7 +51,8 @@ class TileDesc(ctypes.Structure):
                 ("R_w", ctypes.c_double), ("R_b", ctypes.c_double), ("R_sense", ctypes.c_double)]
 
 
-OPTIONS = {"sweep_kernel": 0, "factor_kernel": 1}
+OPTIONS = {"sweep_kernel": 0, "factor_kernel": 1, "algorithm": 2, "cr_products": 3, "wait_limit_ns": 4}
+ALGORITHMS = {"thomas": 0, "cr": 1}
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -150,20 +151,68 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+def _cuda_index(a):
+    """CUDA device index of a torch tensor, or None for host memory (numpy or CPU tensors)."""
+    dev = getattr(a, "device", None)
+    if dev is None or getattr(dev, "type", None) != "cuda":
+        return None
+    return dev.index if dev.index is not None else 0
+
+
+def _check_shape(name, a, shape, device):
+    """Refuse (ValueError) an array whose shape or device does not match what the C call will
+    assume: the library receives a bare pointer and would read or write past its end."""
+    if a is None:
+        return
+    if tuple(int(d) for d in a.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(a.shape)}, expected {tuple(shape)}")
+    idx = _cuda_index(a)
+    if idx is not None and device is not None and idx != device:
+        raise ValueError(f"{name} is on cuda:{idx}, the handle on cuda:{device}")
+
+
+def _current_device():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_device()
+    except ImportError:
+        pass
+    return None
+
+
 @dataclass
 class Crossbar:
     """Handle of one assembled crossbar (xbar_assemble); factor() then solve() any number of batches."""
     M: int
     N: int
     handle: int
+    device: int = None  # CUDA device the handle was created on (None: unknown)
 
     @classmethod
     def assemble(cls, G, Rs, Rw, Rb, Rsense, stream=None):
-        lib = load()
+        if len(G.shape) != 2:
+            raise ValueError(f"G must be M x N, got shape {tuple(G.shape)}")
         M, N = int(G.shape[0]), int(G.shape[1])
+        dev = _cuda_index(G)
+        if dev is None:
+            dev = _current_device()
+        elif dev != _current_device():
+            raise ValueError(f"G is on cuda:{dev}, the current device is cuda:{_current_device()}")
+        lib = load()
         h = _vp()
         _check(lib.xbar_assemble(M, N, _ptr(G), Rs, Rw, Rb, Rsense, _stream_ptr(stream), ctypes.byref(h)))
-        return cls(M, N, h.value)
+        return cls(M, N, h.value, dev)
+
+    def _check_batch(self, V, I, vWL=None, vBL=None):
+        if len(V.shape) != 2:
+            raise ValueError(f"V must be B x M, got shape {tuple(V.shape)}")
+        B = int(V.shape[0])
+        _check_shape("V", V, (B, self.M), self.device)
+        _check_shape("I", I, (B, self.N), self.device)
+        _check_shape("vWL", vWL, (B, self.M, self.N), self.device)
+        _check_shape("vBL", vBL, (B, self.M, self.N), self.device)
+        return B
 
     def factor(self, precision="fp64"):
         _check(load().xbar_factor(self.handle, PRECISIONS.get(precision, precision)))
@@ -171,8 +220,8 @@ class Crossbar:
 
     def solve(self, V, I, vWL=None, vBL=None, tol=1e-8, max_iter=10, raise_on_error=True):
         """xbar_solve: V [B x M] -> I [B x N] (+ node voltages [B x M x N]); returns (status, info dict)."""
+        B = self._check_batch(V, I, vWL, vBL)
         info = SolveInfo()
-        B = int(V.shape[0])
         st = load().xbar_solve(self.handle, B, _ptr(V), _ptr(I), _ptr(vWL), _ptr(vBL), tol, max_iter,
                                ctypes.byref(info))
         if raise_on_error:
@@ -181,7 +230,8 @@ class Crossbar:
 
     def solve_noalloc(self, V, I, raise_on_error=True):
         """xbar_solve_noalloc: FP64 substitution with library-internal fixed scratch (device V, I only)."""
-        st = load().xbar_solve_noalloc(self.handle, int(V.shape[0]), _ptr(V), _ptr(I))
+        B = self._check_batch(V, I)
+        st = load().xbar_solve_noalloc(self.handle, B, _ptr(V), _ptr(I))
         if raise_on_error:
             _check(st)
         return st
@@ -190,6 +240,7 @@ class Crossbar:
         """xbar_transfer_matrix: G_eff (M x N) of the current factorization from M unit solves (cached
         until the next factor); optionally copied into Geff. Returns (status, info dict)."""
         info = SolveInfo()
+        _check_shape("Geff", Geff, (self.M, self.N), self.device)
         st = load().xbar_transfer_matrix(self.handle, tol, max_iter, _ptr(Geff), ctypes.byref(info))
         if raise_on_error:
             _check(st)
@@ -197,17 +248,21 @@ class Crossbar:
 
     def solve_transfer(self, V, I, raise_on_error=True):
         """xbar_solve_transfer: I = V G_eff (currents only), one FP64 product."""
-        st = load().xbar_solve_transfer(self.handle, int(V.shape[0]), _ptr(V), _ptr(I))
+        B = self._check_batch(V, I)
+        st = load().xbar_solve_transfer(self.handle, B, _ptr(V), _ptr(I))
         if raise_on_error:
             _check(st)
         return st
 
     def set_option(self, name, value):
-        """xbar_set_option: 'sweep_kernel' (0 CUDA cores, 1 tensor cores) / 'factor_kernel' (0 group, 1 cluster)."""
+        """xbar_set_option: 'sweep_kernel' (0 CUDA cores, 1 tensor cores) / 'factor_kernel' (0 group,
+        1 cluster) / 'algorithm' (0 or 'thomas', 1 or 'cr') / 'cr_products' (0 CUDA cores, 1 tensor cores)."""
+        value = ALGORITHMS.get(value, value)
         _check(load().xbar_set_option(self.handle, OPTIONS[name], int(value)))
         return self
 
     def set_conductances(self, G):
+        _check_shape("G", G, (self.M, self.N), self.device)
         _check(load().xbar_set_conductances(self.handle, _ptr(G)))
         return self
 

@@ -271,6 +271,32 @@ def pin_zero_parasitic_limit():
         assert 9.0 < r < 11.0, rates
 
 
+def pin_voltage_layout():
+    """vWL[b, i, j] and vBL[b, i, j] are the word-line and bit-line voltages of row i, column j.
+
+    Read against the stamp assembly's own numbering (word-line node i*N+j, bit-line node
+    MN + i*N+j, before its permutation), on crossbars with M != N so that a transposed or
+    swapped layout changes the values.
+    """
+    rng = np.random.default_rng(9)
+    for M, N in [(3, 5), (4, 2)]:
+        G, R = rand_case(rng, M, N)
+        V = rng.uniform(0.05, 0.5, size=(2, M))
+        out = oracle.solve(M, N, G, *R, V, voltages=True)
+        assert out["vWL"].shape == (2, M, N) and out["vBL"].shape == (2, M, N)
+        for b in range(2):
+            As, bs = stamp_dense(M, N, G, *R, V=V[b])
+            x = np.linalg.solve(As, bs)
+            for i in range(M):
+                for j in range(N):
+                    np.testing.assert_allclose(out["vWL"][b, i, j], x[2 * (i * N + j)], rtol=1e-12)
+                    np.testing.assert_allclose(out["vBL"][b, i, j], x[2 * (i * N + j) + 1], rtol=1e-12)
+            # physical orientation: the source end of word line i is column 0; the sense end of
+            # bit line j is row M-1
+            np.testing.assert_allclose((V[b] - out["vWL"][b, :, 0]) / R[0], out["Isrc"][b], rtol=1e-12)
+            np.testing.assert_allclose(out["vBL"][b, M - 1, :] / R[3], out["I"][b], rtol=1e-12)
+
+
 ALL_PINS = [pin_counts, pin_stamp_assembly, pin_paper_equations, pin_dense_bruteforce,
             pin_closed_forms, pin_kirchhoff_linearity_reciprocity, pin_max_principle_rayleigh,
-            pin_zero_parasitic_limit]
+            pin_zero_parasitic_limit, pin_voltage_layout]

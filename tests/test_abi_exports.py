@@ -79,3 +79,39 @@ def test_binding_marshals_only_contiguous_float64():
         xbar._ptr(a[:, ::2])  # not contiguous
     with pytest.raises(TypeError):
         xbar._ptr([1.0, 2.0])
+
+
+def test_injected_allocation_failure_without_gpu(monkeypatch):
+    """XBAR_FAIL_ALLOC_AFTER=0 makes the first device allocation fail before cudaMalloc is called:
+    xbar_assemble returns XBAR_ENOMEM ("out of memory") and no handle."""
+    import numpy as np
+    lib = xbar.load()
+    G = np.full((6, 5), 1e-5)
+    h = ctypes.c_void_p(1234)
+    monkeypatch.setenv("XBAR_FAIL_ALLOC_AFTER", "0")
+    assert lib.xbar_assemble(6, 5, G.ctypes.data, 1, 1, 1, 10, None, ctypes.byref(h)) == xbar.XBAR_ENOMEM
+    assert b"out of memory" in lib.xbar_last_error()
+    assert not h.value
+
+
+def test_binding_refuses_wrong_shapes_without_gpu():
+    """The binding checks array shapes before any pointer reaches the library."""
+    import numpy as np
+    import pytest
+    xb = xbar.Crossbar(4, 3, 0)  # never reaches the library: every call below fails its shape check
+    with pytest.raises(ValueError):
+        xb.solve(np.zeros((2, 5)), np.zeros((2, 3)))
+    with pytest.raises(ValueError):
+        xb.solve(np.zeros((2, 4)), np.zeros((3, 3)))
+    with pytest.raises(ValueError):
+        xb.solve(np.zeros((2, 4)), np.zeros((2, 3)), vWL=np.zeros((2, 3, 4)))
+    with pytest.raises(ValueError):
+        xb.solve_noalloc(np.zeros((2, 4, 1)), np.zeros((2, 3)))
+    with pytest.raises(ValueError):
+        xb.solve_transfer(np.zeros((2, 4)), np.zeros((2, 4)))
+    with pytest.raises(ValueError):
+        xb.transfer_matrix(Geff=np.zeros((3, 4)))
+    with pytest.raises(ValueError):
+        xb.set_conductances(np.zeros((3, 4)))
+    with pytest.raises(ValueError):
+        xbar.Crossbar.assemble(np.zeros(12), 1, 1, 1, 10)

@@ -95,7 +95,7 @@ def test_transfer_state_and_errors():
     st, info2 = xb.transfer_matrix()  # cached: no solves
     assert st == xbar.XBAR_OK and info2["iters"] == 0
     assert xb.solve_transfer(_dev(V), I) == xbar.XBAR_OK
-    assert xb.solve_transfer(_dev(V[:0]), I, raise_on_error=False) == xbar.XBAR_OK  # B = 0
+    assert xb.solve_transfer(_dev(V[:0]), I[:0], raise_on_error=False) == xbar.XBAR_OK  # B = 0
     # new conductances invalidate G_eff until the next factor + transfer_matrix
     G2 = G * 1.5
     xb.set_conductances(_dev(G2))

@@ -40,6 +40,9 @@ MUTANTS = {
     # extraction
     "current_from_top_row": ("I[(size_t)b * N + j] = xb[idx_bl(N, M - 1, j)] / Rsense;",
                              "I[(size_t)b * N + j] = xb[idx_bl(N, 0, j)] / Rsense;"),
+    "voltages_transposed": ("const size_t o = ((size_t)b * M + i) * N + j;",
+                            "const size_t o = ((size_t)b * N + j) * M + i;"),
+    "voltages_wl_bl_swapped": ("if (vWL) vWL[o] = xb[idx_wl(N, i, j)];", "if (vWL) vWL[o] = xb[idx_bl(N, i, j)];"),
 }
 
 
