@@ -67,13 +67,14 @@ struct CrInitParams {
   double gs;
   const double* Coff;  // [N][Mp][Mp] off-diagonal of the column blocks (unscaled)
   const double* h;     // [N][Mp]
-  const double* s;     // [N][Mp] equilibration, or nullptr
+  const T* s;          // [N][Mp] equilibration in the factor's precision, or nullptr
   const T* e;          // [N][Mp] coupling column j -> j+1 (equilibrated if s is set)
   T *D, *gam, *om, *gD;
 };
 
 // D_j (scaled) with its subtraction-free diagonal; gamma, weights w and block leakage gD.
-// Grid (ceil(Mp/8), N), warp per row.
+// Grid (ceil(Mp/8), N), warp per row.  The scales and weights are read in the factor's precision
+// (s32 / its reciprocal for FP32; unscaled for FP64), so the inner loop has no FP64 division.
 template <typename T>
 __global__ void cr_init_kernel(CrInitParams<T> p) {
   const int j = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -82,7 +83,8 @@ __global__ void cr_init_kernel(CrInitParams<T> p) {
   const int M = p.M, Mp = p.Mp, N = p.N;
   const size_t vo = (size_t)j * Mp;
   const bool real = i < M;
-  const double si = (real && p.s) ? p.s[vo + i] : 1.0;
+  const T* s = p.s;  // nullptr: unscaled
+  const T si = (real && s) ? s[vo + i] : (T)1;
   T* Drow = p.D + (vo + i) * Mp;
   const double* Crow = p.Coff + (vo + i) * Mp;
   T off = (T)0;
@@ -90,9 +92,9 @@ __global__ void cr_init_kernel(CrInitParams<T> p) {
     if (m == i) continue;
     T v = (T)0;
     if (real && m < M) {
-      const double sm = p.s ? p.s[vo + m] : 1.0;
-      v = (T)(si * sm * Crow[m]);
-      off += fabs(v) * (T)(1.0 / sm);
+      const T sm = s ? s[vo + m] : (T)1;
+      v = (T)Crow[m] * (si * sm);
+      off += s ? fabs(v) / sm : fabs(v);
     }
     Drow[m] = v;
   }
@@ -100,10 +102,10 @@ __global__ void cr_init_kernel(CrInitParams<T> p) {
   if (lane == 0) {
     T gam = (T)1, om = (T)1, cpl = (T)0;
     if (real) {
-      gam = (T)(si * (p.h[vo + i] + (j == 0 ? p.gs : 0.0)));
-      om = (T)(1.0 / si);
-      if (j > 0) cpl += p.e[vo - Mp + i] * (T)(1.0 / (p.s ? p.s[vo - Mp + i] : 1.0));
-      if (j + 1 < N) cpl += p.e[vo + i] * (T)(1.0 / (p.s ? p.s[vo + Mp + i] : 1.0));
+      gam = si * (T)(p.h[vo + i] + (j == 0 ? p.gs : 0.0));
+      om = s ? (T)1 / si : (T)1;
+      if (j > 0) cpl += s ? p.e[vo - Mp + i] / s[vo - Mp + i] : p.e[vo - Mp + i];
+      if (j + 1 < N) cpl += s ? p.e[vo + i] / s[vo + Mp + i] : p.e[vo + i];
     }
     p.gam[vo + i] = gam;
     p.om[vo + i] = om;
@@ -149,56 +151,92 @@ __global__ void cr_l0_upd_kernel(int Mp, int N, const T* __restrict__ e, const T
 }
 
 // ---- every level: leakage and diagonals of the kept blocks ----------------------------------------
-// One block per kept p (with left/right eliminated neighbours kl, kr and next/previous kept
-// blocks pn, pp of the next level; -1 where absent).
+// Grid (kept blocks, Mp / 64): a block of 1024 threads handles 64 rows i of one kept p (with left /
+// right eliminated neighbours kl, kr and next / previous kept blocks pn, pp of the next level; -1
+// where absent).  Column sums (gamma' and the left coupling's row sums) split the summation index
+// 16 ways with every load of a thread independent; row sums use two warps per row.
+constexpr int kGthThreads = 1024, kGthRows = 64, kGthParts = kGthThreads / kGthRows;
 template <typename T>
-__global__ void __launch_bounds__(256) cr_gth_kernel(int Mp, const CrGthIdx* __restrict__ idx,
-                                                     const T* __restrict__ P, const T* __restrict__ Q, T* gam,
-                                                     const T* __restrict__ om, T* D, const T* __restrict__ U,
-                                                     T* gD) {
-  __shared__ T gs[256], lcs[256];
+__global__ void __launch_bounds__(kGthThreads) cr_gth_kernel(int Mp, const CrGthIdx* __restrict__ idx,
+                                                             const T* __restrict__ P, const T* __restrict__ Q,
+                                                             T* gam, const T* __restrict__ om, T* D,
+                                                             const T* __restrict__ U, T* gD) {
+  __shared__ T gpart[kGthParts][kGthRows], lpart[kGthParts][kGthRows], rpart[2][kGthRows], opart[2][kGthRows];
   const CrGthIdx x = idx[blockIdx.x];
+  const int i0 = blockIdx.y * kGthRows;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const size_t MM = (size_t)Mp * Mp;
-  for (int i = tid; i < Mp; i += blockDim.x) {  // column sums: gamma' and the left coupling row sum
-    T g = gam[(size_t)x.p * Mp + i];
-    if (x.kl >= 0) {
-      const T* Qk = Q + (size_t)x.kl * MM;
-      const T* gk = gam + (size_t)x.kl * Mp;
-      T a = (T)0;
-      for (int m = 0; m < Mp; ++m) a += Qk[(size_t)m * Mp + i] * gk[m];
-      g += a;
+  {
+    const int il = tid % kGthRows, part = tid / kGthRows, i = i0 + il;
+    const int q = (Mp + kGthParts - 1) / kGthParts, m0 = part * q;
+    T g = (T)0, lc = (T)0;
+    if (i < Mp) {
+      // blocks that do not exist are skipped, never read (their storage may hold anything)
+      const bool hl = x.kl >= 0, hr = x.kr >= 0, hu = x.pp >= 0;
+      const T* Qk = Q + (size_t)(hl ? x.kl : 0) * MM;
+      const T* gl = gam + (size_t)(hl ? x.kl : 0) * Mp;
+      const T* Pk = P + (size_t)(hr ? x.kr : 0) * MM;
+      const T* gr = gam + (size_t)(hr ? x.kr : 0) * Mp;
+      const T* Up = U + (size_t)(hu ? x.pp : 0) * MM;
+      const T* wpp = om + (size_t)(hu ? x.pp : 0) * Mp;
+      T sa = (T)0, sb = (T)0, sc = (T)0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {  // fully unrolled: the loads are independent (Mp <= 256: q <= 16)
+        const int m = m0 + u;
+        if (u < q && m < Mp) {
+          if (hl) sa = fma(Qk[(size_t)m * Mp + i], gl[m], sa);
+          if (hr) sb = fma(Pk[(size_t)m * Mp + i], gr[m], sb);
+          if (hu) sc = fma(Up[(size_t)m * Mp + i], wpp[m], sc);
+        }
+      }
+      g = sa + sb;
+      lc = sc;
     }
-    if (x.kr >= 0) {
-      const T* Pk = P + (size_t)x.kr * MM;
-      const T* gk = gam + (size_t)x.kr * Mp;
-      T a = (T)0;
-      for (int m = 0; m < Mp; ++m) a += Pk[(size_t)m * Mp + i] * gk[m];
-      g += a;
-    }
-    T lc = (T)0;
-    if (x.pp >= 0) {
-      const T* Up = U + (size_t)x.pp * MM;
-      const T* w = om + (size_t)x.pp * Mp;
-      for (int m = 0; m < Mp; ++m) lc += Up[(size_t)m * Mp + i] * w[m];
-    }
-    gs[i] = g;
-    lcs[i] = lc;
+    gpart[part][il] = g;
+    lpart[part][il] = lc;
   }
-  __syncthreads();
+  // row sums: two warps per row (32 warps, 64 rows: 4 rows per warp pair)
   const T* wp = om + (size_t)x.p * Mp;
-  for (int i = warp; i < Mp; i += 8) {  // row sums: off-diagonal and right coupling
-    const T* Drow = D + ((size_t)x.p * Mp + i) * Mp;
-    const T* Urow = U + ((size_t)x.p * Mp + i) * Mp;
+  const bool hn = x.pn >= 0;
+  const T* wn = om + (size_t)(hn ? x.pn : 0) * Mp;
+  const int half = warp & 1;
+  for (int il = warp >> 1; il < kGthRows; il += kGthThreads / 64) {
+    const int i = i0 + il;
     T off = (T)0, rc = (T)0;
-    for (int m = lane; m < Mp; m += 32) {
-      if (m != i) off += fabs(Drow[m]) * wp[m];
-      if (x.pn >= 0) rc += Urow[m] * om[(size_t)x.pn * Mp + m];
+    if (i < Mp) {
+      const T* Drow = D + ((size_t)x.p * Mp + i) * Mp;
+      const T* Urow = U + ((size_t)x.p * Mp + i) * Mp;
+      T dv[4], uv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = half * 128 + lane + 32 * u;
+        const bool in = m < Mp;
+        dv[u] = (in && m != i) ? fabs(Drow[m]) * wp[m] : (T)0;
+        uv[u] = (in && hn) ? Urow[m] * wn[m] : (T)0;
+      }
+      off = (dv[0] + dv[1]) + (dv[2] + dv[3]);
+      rc = (uv[0] + uv[1]) + (uv[2] + uv[3]);
     }
     off = cr_warp_sum(off);
     rc = cr_warp_sum(rc);
     if (lane == 0) {
-      const T g = gs[i], gd = g + lcs[i] + rc;
+      opart[half][il] = off;
+      rpart[half][il] = rc;
+    }
+  }
+  __syncthreads();
+  if (tid < kGthRows) {
+    const int i = i0 + tid;
+    if (i < Mp) {
+      T gs = (T)0, ls = (T)0;
+#pragma unroll
+      for (int pt = 0; pt < kGthParts; ++pt) {
+        gs += gpart[pt][tid];
+        ls += lpart[pt][tid];
+      }
+      const T g = gam[(size_t)x.p * Mp + i] + gs;
+      const T gd = g + ls + (rpart[0][tid] + rpart[1][tid]);
+      const T off = opart[0][tid] + opart[1][tid];
       gam[(size_t)x.p * Mp + i] = g;
       gD[(size_t)x.p * Mp + i] = gd;
       D[((size_t)x.p * Mp + i) * Mp + i] = (gd + off) / wp[i];
@@ -207,30 +245,54 @@ __global__ void __launch_bounds__(256) cr_gth_kernel(int Mp, const CrGthIdx* __r
 }
 
 // Diagonal of S = C - B^T W (2 x 2 block inversion of block k, W = A^-1 B <= 0):
-// S w_c = gD_c - W^T gD_a.  One block per eliminated block; ks[jj] = k, W + jj h c.
+// S w_c = gD_c - W^T gD_a.  Grid (eliminated blocks, c / 64): 64 rows of S per block of 1024
+// threads; ks[jj] = k, W + jj h c.
 template <typename T>
-__global__ void __launch_bounds__(256) cr_gth_s_kernel(int Mp, int h, const int* __restrict__ ks,
-                                                       const T* __restrict__ W, T* Dinv,
-                                                       const T* __restrict__ gD, const T* __restrict__ om) {
-  __shared__ T gs[256];
-  const int c = Mp - h, jj = blockIdx.x, k = ks[jj];
+__global__ void __launch_bounds__(kGthThreads) cr_gth_s_kernel(int Mp, int h, const int* __restrict__ ks,
+                                                               const T* __restrict__ W, T* Dinv,
+                                                               const T* __restrict__ gD, const T* __restrict__ om) {
+  __shared__ T gpart[kGthParts][kGthRows], opart[kGthRows];
+  const int c = Mp - h, jj = blockIdx.x, k = ks[jj], i0 = blockIdx.y * kGthRows;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const T* Wk = W + (size_t)jj * h * c;
   const T* g = gD + (size_t)k * Mp;
   const T* w = om + (size_t)k * Mp + h;
-  for (int i = tid; i < c; i += blockDim.x) {
-    T a = g[h + i];
-    for (int m = 0; m < h; ++m) a -= Wk[(size_t)m * c + i] * g[m];
-    gs[i] = a;
+  {
+    const int il = tid % kGthRows, part = tid / kGthRows, i = i0 + il;
+    const int q = (h + kGthParts - 1) / kGthParts, m0 = part * q;  // h <= 128: q <= 8
+    T a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int m = m0 + u;
+      a[u] = (i < c && u < q && m < h) ? Wk[(size_t)m * c + i] * g[m] : (T)0;
+    }
+    gpart[part][il] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  }
+  T* S = Dinv + ((size_t)k * Mp + h) * Mp + h;
+  for (int il = warp; il < kGthRows; il += kGthThreads / 32) {
+    const int i = i0 + il;
+    T off = (T)0;
+    if (i < c) {
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = lane + 32 * u;
+        v[u] = (m < c && m != i) ? fabs(S[(size_t)i * Mp + m]) * w[m] : (T)0;
+      }
+      off = (v[0] + v[1]) + (v[2] + v[3]);
+    }
+    off = cr_warp_sum(off);
+    if (lane == 0) opart[il] = off;
   }
   __syncthreads();
-  T* S = Dinv + ((size_t)k * Mp + h) * Mp + h;
-  for (int i = warp; i < c; i += 8) {
-    T off = (T)0;
-    for (int m = lane; m < c; m += 32)
-      if (m != i) off += fabs(S[(size_t)i * Mp + m]) * w[m];
-    off = cr_warp_sum(off);
-    if (lane == 0) S[(size_t)i * Mp + i] = (gs[i] + off) / w[i];
+  if (tid < kGthRows) {
+    const int i = i0 + tid;
+    if (i < c) {
+      T gs = (T)0;
+#pragma unroll
+      for (int pt = 0; pt < kGthParts; ++pt) gs += gpart[pt][tid];
+      S[(size_t)i * Mp + i] = (g[h + i] - gs + opart[tid]) / w[i];
+    }
   }
 }
 
@@ -576,7 +638,7 @@ cudaError_t cr_factor(xbar_s* hd, CrPlan<T>& pl, bool tensor, bool equilibrate) 
         ip.gs = m.gs;
         ip.Coff = m.Coff;
         ip.h = m.h;
-        ip.s = equilibrate ? m.s_eq : nullptr;
+        ip.s = equilibrate ? (const T*)(const void*)m.s32 : nullptr;  // FP32 factors only
         ip.e = e;
         ip.D = D;
         ip.gam = (T*)pl.gam.p;
@@ -601,13 +663,13 @@ cudaError_t cr_factor(xbar_s* hd, CrPlan<T>& pl, bool tensor, bool equilibrate) 
         err = cudaGetLastError();
         break;
       case CR_OP_GTH:
-        cr_gth_kernel<T><<<o.cnt, 256, 0, st>>>(Mp, (const CrGthIdx*)pl.gidx.p + o.off, (const T*)pl.P.p,
+        cr_gth_kernel<T><<<dim3(o.cnt, (Mp + kGthRows - 1) / kGthRows), kGthThreads, 0, st>>>(Mp, (const CrGthIdx*)pl.gidx.p + o.off, (const T*)pl.P.p,
                                                 (const T*)pl.Q.p, (T*)pl.gam.p, (const T*)pl.om.p, D,
                                                 (const T*)pl.U[o.aux].p, (T*)pl.gD.p);
         err = cudaGetLastError();
         break;
       case CR_OP_GTHS:
-        cr_gth_s_kernel<T><<<o.cnt, 256, 0, st>>>(Mp, o.m, (const int*)pl.ks.p + o.off, (const T*)pl.W.p, Dinv,
+        cr_gth_s_kernel<T><<<dim3(o.cnt, (Mp - o.m + kGthRows - 1) / kGthRows), kGthThreads, 0, st>>>(Mp, o.m, (const int*)pl.ks.p + o.off, (const T*)pl.W.p, Dinv,
                                                   (const T*)pl.gD.p, (const T*)pl.om.p);
         err = cudaGetLastError();
         break;

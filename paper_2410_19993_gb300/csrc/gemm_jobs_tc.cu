@@ -12,11 +12,11 @@
 // FP32-level accuracy, which the factor's refinement relies on; all operands of the factor are
 // entrywise non-negative or non-positive blocks, so no product cancels.
 //
-// Roles (416 threads): warps 0-7 load the FP32 slabs of A (128 rows x 16) and B (TN columns x 16)
-// with coalesced loads for either storage order, split them and store the terms in the no-swizzle
+// Roles: 12 producer warps copy the FP32 slabs of A (128 rows x 16)
+// and B (TN columns x 16) for either storage order, split them and store the terms in the no-swizzle
 // K-major core-matrix layout of the MMA (8 rows x 16 bytes per core matrix) into a ring of stages;
-// warp 8 issues the MMAs from one thread and frees each stage with tcgen05.commit; warps 9-12 drain
-// the accumulator (tcgen05.ld, lane = row), apply C = Cin + alpha D and store.  The accumulator is
+// the next warp issues the MMAs from one thread and frees each stage with tcgen05.commit; the last
+// four drain the accumulator (tcgen05.ld, lane = row), apply C = Cin + alpha D and store.  The accumulator is
 // double-buffered in tensor memory (2 TN columns), so one tile's epilogue overlaps the next tile's
 // MMAs.  Every wait is bounded (XBAR_DEV_TIMEOUT); on expiry a role stops, and the MMA thread waits
 // for its own issued MMAs before the block frees tensor memory.
@@ -30,31 +30,96 @@ namespace xbar {
 
 namespace gtc {
 constexpr int kTM = 128, kKC = 16;
-constexpr int kProd = 8, kEpi = 4;
-constexpr int kThreads = (kProd + 1 + kEpi) * 32;
+constexpr int kEpi = 4;
+// producer warps: the 32-item groups of a chunk (8 of A, TN / 16 of B) are dealt round-robin
+__host__ __device__ constexpr int ngroups(int TN) { return 8 + TN / 16; }
+#ifndef XBAR_GTC_NP256
+#define XBAR_GTC_NP256 12
+#endif
+#ifndef XBAR_GTC_NP128
+#define XBAR_GTC_NP128 12
+#endif
+#ifndef XBAR_GTC_NS256
+#define XBAR_GTC_NS256 3
+#endif
+#ifndef XBAR_GTC_RS256
+#define XBAR_GTC_RS256 2
+#endif
+#ifndef XBAR_GTC_SPIN_NS
+#define XBAR_GTC_SPIN_NS 0
+#endif
+__host__ __device__ constexpr int nprod(int TN) { return TN == 256 ? XBAR_GTC_NP256 : XBAR_GTC_NP128; }
+__host__ __device__ constexpr int nthreads(int TN) { return (nprod(TN) + 1 + kEpi) * 32; }
+__host__ __device__ constexpr int groups_per_warp(int TN) { return (ngroups(TN) + nprod(TN) - 1) / nprod(TN); }
 constexpr uint32_t kAterm = 2 * (kTM / 8) * 128;  // one BF16 term of the A slab: 4 KB
 __host__ __device__ constexpr uint32_t bterm(int TN) { return 2u * (TN / 8) * 128; }
 __host__ __device__ constexpr uint32_t stage_bytes(int TN) { return 3 * kAterm + 3 * bterm(TN); }
-__host__ __device__ constexpr int nstages(int TN) { return TN == 256 ? 5 : 8; }
+__host__ __device__ constexpr int nstages(int TN) { return TN == 256 ? XBAR_GTC_NS256 : 3; }
+// Raw FP32 slabs arrive by cp.async into a ring of RS stages.  Every producer warp has a private
+// slice of each stage: per group of 32 items (rows of A or columns of B) 8 K values each, either as
+// [item][k] at a pitch of 12 floats (K contiguous in the source; the pitch keeps 16-byte reads of
+// consecutive items in different banks) or as [k][item] (items contiguous in the source).  Either
+// order fits the same 384 floats, so a warp never touches another warp's bytes, whichever
+// operand order the chunks of different segments use.
+constexpr int kPitch = 12;
+constexpr uint32_t kGroupFloats = 32 * kPitch;  // >= 8 x 32
+__host__ __device__ constexpr uint32_t warp_raw_floats(int TN) { return kGroupFloats * groups_per_warp(TN); }
+__host__ __device__ constexpr uint32_t raw_bytes(int TN) { return (uint32_t)nprod(TN) * warp_raw_floats(TN) * 4; }
+__host__ __device__ constexpr int rstages(int TN) { return TN == 256 ? XBAR_GTC_RS256 : 3; }
 constexpr uint32_t kHdr = 1024;  // barriers and flags
-__host__ __device__ constexpr size_t smem_bytes(int TN) { return kHdr + (size_t)nstages(TN) * stage_bytes(TN); }
+// epilogue transpose buffers: per epilogue warp 32 rows x 32 columns at a pitch of 36 floats
+constexpr int kEpiPitch = 36;
+constexpr uint32_t kEpiBytes = kEpi * 32 * kEpiPitch * 4;
+__host__ __device__ constexpr size_t smem_bytes(int TN) {
+  return kHdr + (size_t)nstages(TN) * stage_bytes(TN) + (size_t)rstages(TN) * raw_bytes(TN) + kEpiBytes;
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only); src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// named barrier over the 8 producer warps; the _or form also returns whether any thread passed true
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool prod_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// x = x0 + x1 + x2 for 8 values -> three 16-byte rows of BF16
+// x = x0 + x1 + x2 for 8 values -> three 16-byte rows of BF16, each term rounded to nearest (the
+// differences are exact in FP32; |x - x0 - x1 - x2| <= 2^-24 |x| or so).  A pair of elements is
+// converted by one cvt.rn.bf16x2; the FP32 values of the rounded terms are read back from the packed
+// word with a shift and a mask.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 (&o)[3]) {
   uint32_t w[3][4];
 #pragma unroll
   for (int e = 0; e < 8; e += 2) {
-    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[e], v[e + 1]);
-    const float ra = v[e] - __low2float(h0), rb = v[e + 1] - __high2float(h0);
-    const __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
-    const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra - __low2float(h1), rb - __high2float(h1));
-    w[0][e / 2] = *reinterpret_cast<const uint32_t*>(&h0);
-    w[1][e / 2] = *reinterpret_cast<const uint32_t*>(&h1);
-    w[2][e / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+    const uint32_t p0 = bf16x2_rn(v[e], v[e + 1]);
+    const float ra = v[e] - __uint_as_float(p0 << 16), rb = v[e + 1] - __uint_as_float(p0 & 0xffff0000u);
+    const uint32_t p1 = bf16x2_rn(ra, rb);
+    const float sa = ra - __uint_as_float(p1 << 16), sb = rb - __uint_as_float(p1 & 0xffff0000u);
+    w[0][e / 2] = p0;
+    w[1][e / 2] = p1;
+    w[2][e / 2] = bf16x2_rn(sa, sb);
   }
 #pragma unroll
   for (int t = 0; t < 3; ++t) o[t] = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
@@ -63,11 +128,11 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 (&o)[3]) {
 }  // namespace gtc
 
 template <int TN>
-__global__ void __launch_bounds__(gtc::kThreads, 1)
+__global__ void __launch_bounds__(gtc::nthreads(TN), 1)
     gemm_jobs_tc_kernel(const GemmJob<float>* __restrict__ jobs, int njobs, int m, int n, int tiles_n,
                         unsigned* status) {
   using namespace gtc;
-  constexpr int NS = nstages(TN);
+  constexpr int NS = nstages(TN), NP = nprod(TN);
   constexpr uint32_t SB = stage_bytes(TN);
   constexpr uint32_t BT = bterm(TN);
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -88,7 +153,7 @@ __global__ void __launch_bounds__(gtc::kThreads, 1)
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], kProd);
+      mbar_init(&full[s], nprod(TN));
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -113,120 +178,191 @@ __global__ void __launch_bounds__(gtc::kThreads, 1)
     j0 = (r % tiles_n) * TN;
   };
 
-  if (warp < kProd) {
-    // ---- producers: load, split and stage the A and B slabs --------------------------------------
-    // The raw values of the next K slab are loaded before the current one is split and stored, so
-    // their latency overlaps that work and the wait for a free stage.
-    const int pt = tid;  // 0..255
-    struct Pos {
-      int t, s, k0;
+  if (warp < NP) {
+    // ---- producers -------------------------------------------------------------------------------
+    // The chunk's items (A: 128 rows, B: TN columns, each 16 K values) form 32-item groups with one
+    // K octet each: A group a < 8 holds rows 32 (a % 4) .. +31, octet a / 4; B group b holds columns
+    // 32 (b % (TN/32)) .. +31, octet b / (TN/32).  Warp w owns groups w, w + NP, ...: it copies by
+    // cp.async exactly the raw FP32 values of its groups, D = RS - 1 chunks ahead, into its own slice
+    // of raw stage c % RS ([item][k] at a pitch of 12 floats when K is contiguous in the source,
+    // [k][item] otherwise).  Nothing crosses warps, so a warp needs only its own wait_group and
+    // __syncwarp before splitting: the warps run independently.  The split writes three BF16 terms
+    // in the MMA's K-major core-matrix layout; lane 0 of each warp then arrives on the stage's
+    // barrier.
+    constexpr int RS = rstages(TN), D = RS - 1, GPW = groups_per_warp(TN), NG = ngroups(TN);
+    float* raw = reinterpret_cast<float*>(stages + (size_t)NS * SB) + (size_t)warp * warp_raw_floats(TN);
+    constexpr uint32_t RSF = raw_bytes(TN) / 4;  // floats per raw stage (all warps)
+    struct Cursor {
+      int t, s, k0, nseg, K, i0, j0, lda, ldb, ta, tb;
+      const float* A;
+      const float* B;
     };
-    auto valid = [&](const Pos& q) { return q.t < ntiles; };
-    auto next = [&](Pos q) {
-      const GemmJob<float>& jb = jobs[q.t / tpj];
-      q.k0 += kKC;
-      if (q.k0 >= jb.k[q.s]) {
-        q.k0 = 0;
-        if (++q.s >= jb.nseg) {
-          q.s = 0;
-          q.t += gridDim.x;
-        }
-      }
-      return q;
-    };
-    auto load = [&](const Pos& q, float (&av)[8], float (&bv)[TN / 128][8]) {
-      int job, i0, j0;
-      tile_of(q.t, job, i0, j0);
+    auto load_seg = [&](Cursor& q) {
+      int job;
+      tile_of(q.t, job, q.i0, q.j0);
       const GemmJob<float>& jb = jobs[job];
-      const float* A = jb.A[q.s];
-      const float* B = jb.B[q.s];
-      const int lda = jb.lda[q.s], ldb = jb.ldb[q.s], ta = jb.ta[q.s], tb = jb.tb[q.s];
-      {
-        const int r = pt & 127, o = pt >> 7;  // A item: row r, K octet o
-        const int gi = i0 + r, gk = q.k0 + 8 * o;
-        if (gi < m) {
-          if (!ta) {
-            const float4* src = reinterpret_cast<const float4*>(A + (size_t)gi * lda + gk);
-            const float4 x = src[0], y = src[1];
-            av[0] = x.x; av[1] = x.y; av[2] = x.z; av[3] = x.w;
-            av[4] = y.x; av[5] = y.y; av[6] = y.z; av[7] = y.w;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) av[e] = A[(size_t)(gk + e) * lda + gi];
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) av[e] = 0.0f;
-        }
+      q.nseg = jb.nseg;
+      q.K = jb.k[q.s];
+      q.A = jb.A[q.s];
+      q.B = jb.B[q.s];
+      q.lda = jb.lda[q.s];
+      q.ldb = jb.ldb[q.s];
+      q.ta = jb.ta[q.s];
+      q.tb = jb.tb[q.s];
+    };
+    auto advance = [&](Cursor& q) {
+      q.k0 += kKC;
+      if (q.k0 < q.K) return;
+      q.k0 = 0;
+      if (++q.s >= q.nseg) {
+        q.s = 0;
+        q.t += gridDim.x;
       }
+      if (q.t < ntiles) load_seg(q);
+    };
+    // group g -> operand (A: g < 8), first item within the tile, K octet
+    auto group = [&](int g, bool& isA, int& base, int& oc) {
+      isA = g < 8;
+      if (isA) {
+        base = 32 * (g & 3);
+        oc = g >> 2;
+      } else {
+        const int b = g - 8;
+        base = 32 * (b % (TN / 32));
+        oc = b / (TN / 32);
+      }
+    };
+    // Copies of this warp's groups for the chunk at the `ahead` cursor.  Per group and lane two
+    // 16-byte granules: K contiguous in the source -> item 16 u + lane / 2, granule lane % 2 of the
+    // octet, stored [item][k] at a pitch of 12 floats; otherwise K row 4 u + lane / 8, item granule
+    // lane % 8, stored [k][item].  Source addresses are formed once per segment (set_groups) and
+    // advance by a fixed stride per chunk.
+    const float* gptr[GPW][2];
+    long long gstep[GPW];
+    uint32_t gdst[GPW][2], gbytes[GPW][2];
+    auto set_groups = [&](const Cursor& q) {
 #pragma unroll
-      for (int u = 0; u < TN / 128; ++u) {  // B items: column col, K octet o
-        const int item = pt + 256 * u;
-        const int col = item % TN, o = item / TN;
-        const int gj = j0 + col, gk = q.k0 + 8 * o;
-        if (gj < n) {
-          if (tb) {
-            const float4* src = reinterpret_cast<const float4*>(B + (size_t)gj * ldb + gk);
-            const float4 x = src[0], y = src[1];
-            bv[u][0] = x.x; bv[u][1] = x.y; bv[u][2] = x.z; bv[u][3] = x.w;
-            bv[u][4] = y.x; bv[u][5] = y.y; bv[u][6] = y.z; bv[u][7] = y.w;
+      for (int gi = 0; gi < GPW; ++gi) {
+        const int g = warp + NP * gi;
+        bool isA;
+        int base, oc;
+        group(g < NG ? g : 0, isA, base, oc);
+        const float* src = isA ? q.A : q.B;
+        const int ld = isA ? q.lda : q.ldb;
+        const int kcontig = isA ? !q.ta : q.tb;
+        const int first = (isA ? q.i0 : q.j0) + base, nitems = isA ? m : n;
+        gstep[gi] = kcontig ? kKC : (long long)kKC * ld;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (kcontig) {
+            const int it = 16 * u + (lane >> 1), kg = lane & 1, x = first + it;
+            gptr[gi][u] = src + (size_t)(x < nitems ? x : 0) * ld + q.k0 + 8 * oc + 4 * kg;
+            gdst[gi][u] = it * kPitch + 4 * kg;
+            gbytes[gi][u] = x < nitems ? 16u : 0u;
           } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) bv[u][e] = B[(size_t)(gk + e) * ldb + gj];
+            const int e = 4 * u + (lane >> 3), ig = lane & 7, x = first + 4 * ig;
+            gptr[gi][u] = src + (size_t)(q.k0 + 8 * oc + e) * ld + (x < nitems ? x : 0);
+            gdst[gi][u] = e * 32 + 4 * ig;
+            gbytes[gi][u] = x < nitems ? 16u : 0u;
           }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) bv[u][e] = 0.0f;
         }
       }
     };
+    auto issue = [&](const Cursor& q, int rs) {
+      if (q.t >= ntiles) return;
+      float* w = raw + (size_t)rs * RSF;
+#pragma unroll
+      for (int gi = 0; gi < GPW; ++gi) {
+        if (warp + NP * gi >= NG) break;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          cp_async16(w + kGroupFloats * gi + gdst[gi][u], gptr[gi][u], gbytes[gi][u]);
+          gptr[gi][u] += gstep[gi];
+        }
+      }
+    };
+    // the ahead cursor: a new segment or tile re-forms the group addresses
+    auto advance_ahead = [&](Cursor& q) {
+      const int s0 = q.s, t0 = q.t;
+      advance(q);
+      if (q.t < ntiles && (q.s != s0 || q.t != t0)) set_groups(q);
+    };
+    // the 8 K values of this lane's item in a group (layout as copied)
+    auto read_group = [&](const float* src, int kcontig, float (&v)[8]) {
+      if (kcontig) {
+        const float4 x = *reinterpret_cast<const float4*>(src + lane * kPitch);
+        const float4 y = *reinterpret_cast<const float4*>(src + lane * kPitch + 4);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w; v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = src[e * 32 + lane];
+      }
+    };
+    Cursor ahead;
+    ahead.t = blockIdx.x;
+    ahead.s = 0;
+    ahead.k0 = 0;
+    if (ahead.t < ntiles) {
+      load_seg(ahead);
+      set_groups(ahead);
+    }
+    Cursor cur = ahead;
+#pragma unroll 1
+    for (int r = 0; r < D; ++r) {
+      issue(ahead, r);
+      cp_async_commit();
+      if (ahead.t < ntiles) advance_ahead(ahead);
+    }
     int st = 0, use = 0;
     long long c = 0;
-    Pos cur{(int)blockIdx.x, 0, 0};
-    float av[8], bv[TN / 128][8], av2[8], bv2[TN / 128][8];
-    if (valid(cur)) load(cur, av, bv);
-    while (valid(cur)) {
-      const Pos nx = next(cur);
-      if (valid(nx)) load(nx, av2, bv2);
-      if (c >= NS && !mbar_spin_bounded(&empty[st], (unsigned)((use - 1) & 1), status, limit, 32)) {
+    while (cur.t < ntiles) {
+      issue(ahead, (int)((c + D) % RS));  // this warp's slice, last read while splitting chunk c - 1
+      cp_async_commit();
+      if (ahead.t < ntiles) advance_ahead(ahead);
+      cp_async_wait<D>();  // this lane's copies of chunk c have landed
+      __syncwarp();        // ... and every lane's, visible to the whole warp
+      bool ok = true;
+      if (lane == 0 && c >= NS)
+        ok = mbar_spin_bounded(&empty[st], (unsigned)((use - 1) & 1), status, limit, XBAR_GTC_SPIN_NS);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok || *fail) {
         *fail = 1;
         break;
       }
-      if (*fail) break;
+      const float* w = raw + (size_t)(c % RS) * RSF;
       unsigned char* sb = stages + (size_t)st * SB;
-      {
-        const int r = pt & 127, o = pt >> 7;
-        uint4 w[3];
-        split8(av, w);
-        const uint32_t off = (uint32_t)o * (kTM / 8) * 128 + (uint32_t)(r >> 3) * 128 + (uint32_t)(r & 7) * 16;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4*>(sb + q * kAterm + off) = w[q];
-      }
+      for (int gi = 0; gi < GPW; ++gi) {
+        const int g = warp + NP * gi;
+        if (g >= NG) break;
+        bool isA;
+        int base, oc;
+        group(g, isA, base, oc);
+        const int it = base + lane;  // this lane's item (row of A or column of B)
+        float v[8];
+        read_group(w + kGroupFloats * gi, isA ? !cur.ta : cur.tb, v);
+        uint4 t3[3];
+        split8(v, t3);
+        if (isA) {
+          const uint32_t off = (uint32_t)oc * (kTM / 8) * 128 + (uint32_t)(it >> 3) * 128 + (uint32_t)(it & 7) * 16;
 #pragma unroll
-      for (int u = 0; u < TN / 128; ++u) {
-        const int item = pt + 256 * u;
-        const int col = item % TN, o = item / TN;
-        uint4 w[3];
-        split8(bv[u], w);
-        const uint32_t off =
-            3 * kAterm + (uint32_t)o * (TN / 8) * 128 + (uint32_t)(col >> 3) * 128 + (uint32_t)(col & 7) * 16;
+          for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4*>(sb + q * kAterm + off) = t3[q];
+        } else {
+          const uint32_t off =
+              3 * kAterm + (uint32_t)oc * (TN / 8) * 128 + (uint32_t)(it >> 3) * 128 + (uint32_t)(it & 7) * 16;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4*>(sb + off + q * BT) = w[q];
+          for (int q = 0; q < 3; ++q) *reinterpret_cast<uint4*>(sb + off + q * BT) = t3[q];
+        }
       }
       fence_proxy_async_smem();
-      __syncwarp();
+      __syncwarp();  // the warp's reads of its raw slice and its BF16 stores are done
       if (lane == 0) mbar_arrive(&full[st]);
       if (++st == NS) { st = 0; ++use; }
       ++c;
-      cur = nx;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) av[e] = av2[e];
-#pragma unroll
-      for (int u = 0; u < TN / 128; ++u)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) bv[u][e] = bv2[u][e];
+      advance(cur);
     }
-  } else if (warp == kProd) {
+    cp_async_wait<0>();  // no copy of this block may still be in flight when it exits
+  } else if (warp == NP) {
     // ---- MMA issuer --------------------------------------------------------------------------------
     if (lane == 0) {
       constexpr uint32_t idesc = umma::idesc_bf16(kTM, TN);
@@ -247,7 +383,7 @@ __global__ void __launch_bounds__(gtc::kThreads, 1)
         bool first = true;
         for (int s = 0; s < jb.nseg && ok; ++s) {
           for (int k0 = 0; k0 < jb.k[s]; k0 += kKC) {
-            if (!mbar_spin_bounded(&full[st], (unsigned)(use & 1), status, limit, 0) || *fail) {
+            if (!mbar_spin_bounded(&full[st], (unsigned)(use & 1), status, limit, XBAR_GTC_SPIN_NS) || *fail) {
               ok = false;
               break;
             }
@@ -285,8 +421,10 @@ __global__ void __launch_bounds__(gtc::kThreads, 1)
     __syncwarp();
   } else {
     // ---- epilogue: TMEM lane quarter (warp % 4) = 32 rows of the tile ------------------------------
+    // Each 32 x 32 block of the accumulator goes through this warp's shared-memory buffer, so that
+    // C (and Cin) are accessed as 4 rows x 128 contiguous bytes per warp instruction.
     const int quarter = warp & 3;
-    const int r = quarter * 32 + lane;
+    float* tb32 = reinterpret_cast<float*>(smem + smem_bytes(TN) - kEpiBytes) + (warp - NP - 1) * 32 * kEpiPitch;
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       int job, i0, j0;
@@ -295,32 +433,41 @@ __global__ void __launch_bounds__(gtc::kThreads, 1)
       const int ab = lt & 1;
       if (!mbar_spin_bounded(&tfull[ab], (unsigned)((lt >> 1) & 1), status, limit, 64) || *fail) break;
       umma::fence_after();
-      const int gi = i0 + r;
       const float alpha = jb.alpha;
-      float* crow = jb.C + (size_t)gi * jb.ldc;
-      const float* cin = jb.Cin ? jb.Cin + (size_t)gi * jb.ldcin : nullptr;
+      float* C = jb.C;
+      const float* Cin = jb.Cin;
+      const int ldc = jb.ldc, ldcin = jb.ldcin;
+      const int rsub = lane >> 3, c4 = (lane & 7) * 4;  // transposed access: row 4 it + rsub, columns c4..c4+3
 #pragma unroll 1
       for (int cc = 0; cc < TN; cc += 32) {
         float v[32];
         umma::ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * TN + cc), v);
-        const int gj = j0 + cc;
-        if (gi < m) {
-          if (gj + 32 <= n) {
 #pragma unroll
-            for (int e = 0; e < 32; e += 4) {
-              float4 o = make_float4(alpha * v[e], alpha * v[e + 1], alpha * v[e + 2], alpha * v[e + 3]);
-              if (cin) {
-                const float4 ci = *reinterpret_cast<const float4*>(cin + gj + e);
+        for (int e = 0; e < 32; e += 4)
+          *reinterpret_cast<float4*>(tb32 + lane * kEpiPitch + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        __syncwarp();
+        const int gj = j0 + cc + c4;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int r = 4 * it + rsub, gi = i0 + quarter * 32 + r;
+          const float4 a = *reinterpret_cast<const float4*>(tb32 + r * kEpiPitch + c4);
+          if (gi < m) {
+            if (gj + 4 <= n) {
+              float4 o = make_float4(alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w);
+              if (Cin) {
+                const float4 ci = *reinterpret_cast<const float4*>(Cin + (size_t)gi * ldcin + gj);
                 o.x += ci.x; o.y += ci.y; o.z += ci.z; o.w += ci.w;
               }
-              *reinterpret_cast<float4*>(crow + gj + e) = o;
-            }
-          } else {
+              *reinterpret_cast<float4*>(C + (size_t)gi * ldc + gj) = o;
+            } else {
+              const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
-              if (gj + e < n) crow[gj + e] = alpha * v[e] + (cin ? cin[gj + e] : 0.0f);
+              for (int e = 0; e < 4; ++e)
+                if (gj + e < n) C[(size_t)gi * ldc + gj + e] = alpha * av[e] + (Cin ? Cin[(size_t)gi * ldcin + gj + e] : 0.0f);
+            }
           }
         }
+        __syncwarp();  // the buffer is rewritten by the next block
       }
       umma::fence_before();
       __syncwarp();
@@ -346,7 +493,8 @@ cudaError_t launch_gemm_jobs_tc(const GemmJob<float>* jobs_dev, int njobs, int m
   auto kern = tn == 256 ? gemm_jobs_tc_kernel<256> : gemm_jobs_tc_kernel<128>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<grid, gtc::kThreads, smem, st>>>(jobs_dev, njobs, m, n, tiles_n, status);
+  kern<<<grid, tn == 256 ? gtc::nthreads(256) : gtc::nthreads(128), smem, st>>>(jobs_dev, njobs, m, n, tiles_n,
+                                                                                status);
   return cudaGetLastError();
 }
 
