@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=64, help="vectors the CPU oracle substitutes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-factor-rates", action="store_true", help="skip the standalone factor timings")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch size (profiling runs)")
     ap.add_argument("--epochs", type=int, default=24, help="surrogate workload: training epochs")
     ap.add_argument("--line-passes", type=int, default=2, help="surrogate workload: line-model passes")
@@ -340,6 +341,11 @@ def run_xbar(args):
                "ms_per_step": 1e3 * t_e2e / args.steps}
         assert np.array_equal(Ih.numpy(), I_mixed), "host-buffer solve differs from device-buffer solve"
 
+    # factorizations/s of each factor (one handle, one map at a time, nothing overlapped) and the
+    # latency of one map's solve for 1 and 16 input vectors right after it (the paper's
+    # decomposition/solve split at small batches)
+    factorizations = factor_rates(xbar, torch, Gd, Vd, R, N, d) if not args.no_factor_rates else None
+
     # per-phase kernel times inside the timed region, and the roofline of the dominant kernel
     per_step = {ph: {"launches": v["launches"] / args.steps, "ms": v["ms"] / args.steps}
                 for ph, v in prof.items() if v["launches"]}
@@ -367,17 +373,29 @@ def run_xbar(args):
         bound, peak, note = "alu", peaks["fp64_tflops"], "FP64 FMA pipe, 152 SM x 2 DFMA x 2 x max SM clock"
     traffic, traffic_note = None, None
     if dom == "sweep" and (M, N) == (256, 256) and bound == "tensor":
-        # ncu DRAM read + write per sweep_tc_kernel launch at B = 2048, averaged over the solve's
-        # launches (2.263 GB initial, 2.212 GB per correction), scaled by the vectors of this launch:
-        # the kernel's streams are per vector
-        traffic = 2.229e9 * B / 2048
-        traffic_note = ("ncu dram__bytes_read+write at B=2048, mean of the solve's three sweep launches, scaled by B "
-                        "(profiles/sweep_tc_xbar256_B2048.md)")
+        # ncu DRAM read + write per sweep_tc_kernel launch at B = 2048 (the capture fits the size
+        # rule; the full batch does not), averaged over the solve's launches (2.261 GB initial,
+        # 2.211 and 2.208 GB for the corrections), scaled by B / 2048: the kernel's streams are per
+        # vector, the factor blocks it re-reads come from L2
+        traffic = 2.227e9 * B / 2048
+        traffic_note = (f"ncu dram__bytes_read+write at B=2048 (mean of the solve's three sweep launches) "
+                        f"x B/2048 = {B / 2048:g}")
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note, "peak_note": note,
                 "work_per_launch": work, "ms_per_launch": ms_launch,
                 "selection": "largest phase on the solve's stream (the critical path); the next map's assembly "
                              "and factor overlap it on the second stream"}
+    if dom == "sweep" and bound == "tensor":
+        # Above ~0.6 PF of BF16 the substitution is HBM-bound: its algorithmic bytes per input vector
+        # are V and I in FP64 and the forward results written and read back in FP32,
+        # 8M + 8N + 2 (2MN 4).  The HBM roof is the primary one; the tensor reading stays beside it.
+        hbm_bytes = B * (8.0 * M + 8.0 * N + 2.0 * (2.0 * M * N * 4.0))
+        hbm_peak = mp.get("hbm_gbs", 6780.0)
+        hbm_achieved = hbm_bytes / (ms_launch / 1e3) / 1e9
+        tensor = {k: roofline[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_note")}
+        roofline.update({"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_achieved / hbm_peak, "bytes_per_launch": hbm_bytes,
+                         "peak_note": "measured copy bandwidth (of measured)", "tensor": tensor})
 
     cpu = None
     err_vs_oracle = None
@@ -408,6 +426,7 @@ def run_xbar(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "factorizations": factorizations,
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -416,6 +435,57 @@ def run_xbar(args):
     for x in xbs:
         x.destroy()
     d.close()
+
+
+def factor_rates(xbar, torch, Gd, Vd, R, N, d):
+    """Standalone factor time per algorithm and precision, and the solve latency that follows.
+
+    One handle on the current stream; each factor is timed alone (K back-to-back factors between
+    CUDA events after a warm-up), so these are the absolute factorizations/s of one map, not the
+    overlapped figure of the two-maps-in-flight schedule."""
+    variants = [("thomas_fp32", "thomas", "fp32_ir", -1), ("cr_fp32_tensor", "cr", "fp32_ir", 1),
+                ("cr_fp32_cuda_cores", "cr", "fp32_ir", 0), ("thomas_fp64", "thomas", "fp64", -1),
+                ("cr_fp64", "cr", "fp64", -1)]
+    out = {}
+    xb = xbar.Crossbar.assemble(Gd, *R)
+    stream = torch.cuda.current_stream()
+
+    def events_ms(fn, K):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    for name, algo, prec, prod in variants:
+        xb.set_option("algorithm", algo)
+        xb.set_option("cr_products", prod)
+        xb.factor(prec)
+        xb.sync()
+        K = 3 if prec == "fp64" else 10
+        ms = d.max(events_ms(lambda: xb.factor(prec), K))
+        rec = {"algorithm": algo, "precision": prec, "factor_ms": ms, "factorizations_per_s": 1e3 / ms,
+               "products": {1: "tensor cores (tcgen05, three-term BF16)", 0: "CUDA cores"}.get(prod, "CUDA cores")}
+        for Bs in (1, 16):
+            Ib = torch.zeros((Bs, N), dtype=torch.float64, device="cuda")
+            xb.solve(Vd[:Bs], Ib, tol=TOL, max_iter=10)
+            xb.sync()
+            box = {}
+
+            def one():
+                _, info = xb.solve(Vd[:Bs], Ib, tol=TOL, max_iter=10)
+                box.update(info)
+
+            rec[f"solve_ms_B{Bs}"] = d.max(events_ms(one, 3))
+            rec[f"iters_B{Bs}"] = box.get("iters")
+        out[name] = rec
+    xb.destroy()
+    out["note"] = ("one 256x256 map at a time: factor_ms = mean of back-to-back factors (CUDA events); "
+                   "solve_ms_B* = one xbar_solve (all refinement) of 1 or 16 vectors after it")
+    return out
 
 
 def run_transfer(args):

@@ -6,7 +6,8 @@
 // solved alone with device i driven by V_i tau(i, j).  It is linear in V:
 //     I_line = V T_line,   T_line(i, j) = tau(i, j) G(i, j) g_o x_j(i),
 // x_j solving bit line j's chain for a unit current at its bottom node.  Both chains are walked
-// once from their open end with subtraction-free ratio recurrences (one thread per line, FP64).
+// once from their open end with subtraction-free ratio recurrences in FP32 (one thread per line
+// for the per-map factors; the unit-input responses walk the chains in shared memory).
 //
 // Network: for bit line j of map G and input vector V it reads 3M features
 //     x = [ G(:,j) / g_scale,  V / v_scale,  S(:,j) / (N g_scale) ],  S(i, j) = sum_{l>=j} G(i, l)
