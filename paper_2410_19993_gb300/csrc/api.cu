@@ -196,6 +196,10 @@ static int cr_sweep_launches(const xbar_s* h, int B, bool initial) {
 // proved too coarse to certify convergence.  Any later correction (slow convergence) and the
 // initial solve use all three (FP32-level accuracy).
 static int correction_terms(int it) { return it < 2 ? 2 : 3; }
+// The initial solve's error is set by the FP32 factor (~1e-4..1e-3 relative at 256 x 256), far
+// above what the two leading BF16 terms of the factor blocks add (~2^-17 per product): the third
+// term would only lengthen the sweep's operand stream.
+constexpr int kInitialTerms = 2;
 
 // Kernel variants.  FP32 substitutions run on the tensor cores (sweep_tc.cu) when the block fits
 // (Mp <= 256) and FP32 factors on a thread-block cluster (factor_cluster.cu) when 32 <= Mp <= 256,
@@ -546,7 +550,7 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       sp.w = nullptr;
       sp.w2out = rp.w2;
       sp.s32 = m.s32;
-      XB_CUDA(launch_sweep_tc(sp, h->Xt.p, 3, st));
+      XB_CUDA(launch_sweep_tc(sp, h->Xt.p, kInitialTerms, st));
       sp.w = (float*)h->dhat.p;
       sp.w2out = nullptr;
     } else {
@@ -696,11 +700,11 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
     sp.w = nullptr;
     sp.w2out = rp.w2;
     sp.s32 = m.s32;
-    XB_CUDA(sweep(3));
+    XB_CUDA(sweep(kInitialTerms));
     sp.w = (float*)h->dhat.p;
     sp.w2out = nullptr;
   } else {
-    XB_CUDA(sweep(3));                   // x0 = solve32(b)
+    XB_CUDA(sweep(kInitialTerms));       // x0 = solve32(b)
     XB_CUDA(launch_update(rp, 1, st));   // w = s o dhat, I = h . w
   }
   sp.V = nullptr;

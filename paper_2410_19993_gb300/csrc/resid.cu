@@ -122,9 +122,11 @@ __global__ void resid_kernel(ResidParams p) {
     p.rhat[o] = rf * p.s32[base + i];
   }
   if (!(rmax <= 3.0e38f)) set_status(p.status, XBAR_DEV_NONFINITE);
-  // block max of |r| then one atomic (non-negative doubles order like their bit patterns)
-  for (int off = 16; off > 0; off >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
-  if ((threadIdx.x & 31) == 0 && p.rmax)
+  // warp max of |r| over the lanes still running (those past Bpad have left), then one atomic per
+  // warp: non-negative floats and doubles order like their bit patterns
+  const unsigned live = __activemask();
+  rmax = __uint_as_float(__reduce_max_sync(live, __float_as_uint(rmax)));
+  if ((threadIdx.x & 31) == __ffs(live) - 1 && p.rmax)
     atomicMax(p.rmax, (unsigned long long)__double_as_longlong((double)rmax));
 }
 

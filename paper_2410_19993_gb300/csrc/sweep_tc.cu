@@ -6,9 +6,10 @@
 // for a panel of 64 input vectors per block.  Each step is D[Mt x 64] = X_j[Mt x Mt] . v[Mt x 64]
 // computed from three-term BF16 splits (x = x0 + x1 + x2, each BF16: together 24+ significant bits,
 // FP32-level accuracy; a plain BF16 or TF32 product would cost the refinement extra passes).  With
-// v0 | v1 | v2 stacked along N, each K step of 16 issues A0 [v0 v1 v2] (N = 192), A1 [v0 v1]
-// (N = 128) and A2 [v0] (N = 64) into one FP32 accumulator, and the epilogue adds its three column
-// blocks: (A0 + A1 + A2)(v0 + v1 + v2) without A1 v2, A2 v1, A2 v2 (each below 2^-26 relative).
+// KP leading terms used, each K step of 16 issues A_p v_q for every p + q < KP (N = 64 each) into
+// one FP32 accumulator: (A0 + A1 + A2)(v0 + v1 + v2) without A1 v2, A2 v1, A2 v2 (each below
+// 2^-26 relative) for KP = 3, A0 v0 + A0 v1 + A1 v0 (~2^-17) for KP = 2.  One accumulator leaves
+// the epilogue a single tensor-memory read per column block on its critical path.
 // Against a split-TF32 product (x = hi + lo, four K=8 products per 16 K) this moves 6 instead of
 // 8 bytes per element of X_j, issues 96 instead of 128 MMAs per step and does 25% less tensor work.
 //
@@ -54,9 +55,8 @@ constexpr int kThreads = 256;
 // node groups of 8 are 128 bytes apart, column groups (Mt/8)*128 bytes apart
 __host__ __device__ constexpr uint32_t lbo_b(int Mt) { return (uint32_t)(Mt / 8) * 128; }  // column-group stride
 // tensor-memory columns for NH halves of KP * 64 columns (allocations are powers of two >= 32)
-__host__ __device__ constexpr uint32_t tmem_cols(int NH, int KP) {
-  return NH * KP * kBP <= 64 ? 64u : NH * KP * kBP <= 128 ? 128u : NH * KP * kBP <= 256 ? 256u : 512u;
-}
+// two accumulators (steps alternate) of NH x 64 columns each
+__host__ __device__ constexpr uint32_t tmem_cols(int NH) { return NH == 1 ? 128u : 256u; }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
@@ -194,10 +194,11 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   constexpr int cps = Mt / KC;  // chunks per step
   const int nsteps = 2 * N - 1;
   const long long nchunks = (long long)nsteps * cps;
-  // accumulators: per 128-row half, KP * 64 columns [X v0 | X v1 | X v2] (tensor memory is allocated in
-  // powers of two)
-  constexpr uint32_t ncols = tmem_cols(NH, KP);
-  constexpr int dcols = KP * BP;
+  // accumulators: per 128-row half, 64 columns; two sets, for even and odd steps, so that the
+  // epilogue can re-read this step's D while the next step's MMAs accumulate into the other set
+  constexpr uint32_t ncols = tmem_cols(NH);
+  constexpr int dcols = BP;
+  constexpr uint32_t dset = NH * dcols;
   constexpr uint32_t copy_bytes = KP * part_bytes;  // leading KP terms of each chunk
   constexpr uint32_t kBMajorMN = 1u << 16;          // instruction descriptor: B is MN-major
   constexpr uint32_t LBO_A = (uint32_t)(Mt / 8) * 128, SBO = 128;
@@ -258,6 +259,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       // 8 nodes (K), the stride byte offset the stride between groups of 8 columns (N)
       const uint64_t bdesc0 = umma::sdesc(smem_addr(vb), 128, LBO_B);
       constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_part = part_bytes >> 4;
+      constexpr uint64_t b_term = ((uint64_t)(kBP / 8) * LBO_B) >> 4;  // v_q: 8 column groups per term
       uint64_t ast = adesc0;  // descriptor of stage mst
       for (int s = 0; s < nsteps; ++s) {
         bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, wlim, 0);
@@ -269,13 +271,14 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
             break;
           }
           fence_after();
-          const uint32_t acc = kc > 0 ? 1u : 0u;
 #pragma unroll
-          for (int pt = 0; pt < KP; ++pt)  // A_pt [v_0 .. v_(KP-1-pt)]: A0 [v0 v1 v2], A1 [v0 v1], A2 [v0]
+          for (int pt = 0; pt < KP; ++pt)  // A_pt v_q for pt + q < KP, all into the one accumulator
 #pragma unroll
-            for (int hh = 0; hh < NH; ++hh)
-              umma::mma_bf16(tbase + hh * dcols, ast + pt * a_part + hh * a_half, bdesc,
-                             umma::idesc_bf16(128, BP * (KP - pt)) | kBMajorMN, pt == 0 ? acc : 1u);
+            for (int qv = 0; qv + pt < KP; ++qv)
+#pragma unroll
+              for (int hh = 0; hh < NH; ++hh)
+                umma::mma_bf16(tbase + (s & 1) * dset + hh * dcols, ast + pt * a_part + hh * a_half, bdesc + qv * b_term,
+                               umma::idesc_bf16(128, BP) | kBMajorMN, (kc > 0 || pt > 0 || qv > 0) ? 1u : 0u);
           mma_commit(&empty[mst]);
           bdesc += (uint64_t)((2 * 128) >> 4);
           ast += a_stage;
@@ -371,6 +374,39 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
                             : 0.0f;
       const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
       const float sj = (real && p.w2out) ? p.s32[(size_t)j * Mp + i] : 0.0f;
+      const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
+      const bool have_w = !fwd || s == N - 1;
+      const bool more = s + 1 < nsteps;
+      // the next input's operands that do not depend on D -- z of this step (back substitution) or
+      // the next column's right-hand side (forward) -- are loaded before the wait: column block 0
+      // now, block 1 right after it, so their latency leaves the step's critical path
+      const bool use_z = !fwd && real;
+      const bool use_r = more && nfwd && p.rhs && real;
+      float pre[ncb][32];
+      auto load_pre = [&](int blk) {
+        if (use_z) {
+          const float4* zrow = reinterpret_cast<const float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;
+#pragma unroll
+          for (int n = 0; n < 32; n += 4) {
+            const float4 zz = zrow[(size_t)(n / 4) * Mp];
+            pre[blk][n] = zz.x;
+            pre[blk][n + 1] = zz.y;
+            pre[blk][n + 2] = zz.z;
+            pre[blk][n + 3] = zz.w;
+          }
+        } else if (use_r) {
+          const float* rn = p.rhs + rowoff + blk * 32 + (size_t)Mp * Bpad;
+#pragma unroll
+          for (int n = 0; n < 32; n += 4) {
+            const float4 r4 = *reinterpret_cast<const float4*>(rn + n);
+            pre[blk][n] = r4.x;
+            pre[blk][n + 1] = r4.y;
+            pre[blk][n + 2] = r4.z;
+            pre[blk][n + 3] = r4.w;
+          }
+        }
+      };
+      load_pre(0);
       // one thread polls the accumulator barrier; the others wait on the named hardware barrier so
       // that no shared-memory polling competes with the tensor core's operand reads
       bool okd = true;
@@ -378,58 +414,26 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       if (!okd) atomicExch(fail, 1u);
       if (epi_sync_or(*fail != 0)) break;
       fence_after();
+#pragma unroll
+      for (int blk = 1; blk < ncb; ++blk) load_pre(blk);
 
-      const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
-      const bool have_w = !fwd || s == N - 1;
-      // (1) D of this step, both column blocks, and z added in the back substitution
-      float a[ncb][32];
-#pragma unroll
-      for (int blk = 0; blk < ncb; ++blk) {
-        float a2[32];
-        const uint32_t t0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * dcols + cb + blk * 32);
-        tmem_ld32(t0, a[blk]);
-#pragma unroll
-        for (int part = 1; part < KP; ++part) {  // the X v1 and X v2 column blocks
-          tmem_ld32(t0 + (uint32_t)part * BP, a2);
-#pragma unroll
-          for (int n = 0; n < 32; ++n) a[blk][n] += a2[n];
-        }
-        if (!fwd && real) {
-          const float4* zrow = reinterpret_cast<const float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;
-#pragma unroll
-          for (int n = 0; n < 32; n += 4) {
-            const float4 zz = zrow[(size_t)(n / 4) * Mp];
-            a[blk][n] += zz.x;
-            a[blk][n + 1] += zz.y;
-            a[blk][n + 2] += zz.z;
-            a[blk][n + 3] += zz.w;
-          }
-        }
-      }
-      // (2) the next step's input, split into hi/lo; then the next step's MMAs may start
-      if (s + 1 < nsteps) {
+      // (1) D of this step per column block (z added in the back substitution), then (2) the next
+      // step's input from it, split into BF16 terms; then the next step's MMAs may start
+      const uint32_t tstep = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((s & 1) * dset + h * dcols + cb);
+      if (more) {
 #pragma unroll
         for (int blk = 0; blk < ncb; ++blk) {
-          if (nfwd && p.rhs && real) {
-            const float* rn = p.rhs + rowoff + blk * 32 + (size_t)Mp * Bpad;
+          float a[32];
+          tmem_ld32(tstep + blk * 32, a);
 #pragma unroll
-            for (int n = 0; n < 32; n += 8) {
-              const float4 r4 = *reinterpret_cast<const float4*>(rn + n);
-              const float4 r5 = *reinterpret_cast<const float4*>(rn + n + 4);
-              const float v[8] = {fmaf(ej, a[blk][n], r4.x),     fmaf(ej, a[blk][n + 1], r4.y),
-                                  fmaf(ej, a[blk][n + 2], r4.z), fmaf(ej, a[blk][n + 3], r4.w),
-                                  fmaf(ej, a[blk][n + 4], r5.x), fmaf(ej, a[blk][n + 5], r5.y),
-                                  fmaf(ej, a[blk][n + 6], r5.z), fmaf(ej, a[blk][n + 7], r5.w)};
-              put_v8(cb + blk * 32 + n, v);
+          for (int n = 0; n < 32; n += 8) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float x = use_z ? a[n + e] + pre[blk][n + e] : a[n + e];
+              v[e] = use_r ? fmaf(ej, x, pre[blk][n + e]) : ej * x;
             }
-          } else {
-#pragma unroll
-            for (int n = 0; n < 32; n += 8) {
-              float v[8];
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v[e] = ej * a[blk][n + e];
-              put_v8(cb + blk * 32 + n, v);
-            }
+            put_v8(cb + blk * 32 + n, v);
           }
         }
         release_v();
@@ -439,25 +443,30 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 #pragma unroll
       for (int blk = 0; blk < ncb; ++blk) {
         const size_t o = rowoff + blk * 32;
+        float a[32];  // this step's D again (its accumulator set is not written until step s + 2)
+        tmem_ld32(tstep + blk * 32, a);
+        if (use_z)
+#pragma unroll
+          for (int n = 0; n < 32; ++n) a[n] += pre[blk][n];
         if (fwd && real) {
           float4* zrow = reinterpret_cast<float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;
 #pragma unroll
           for (int n = 0; n < 32; n += 4)
-            zrow[(size_t)(n / 4) * Mp] = make_float4(a[blk][n], a[blk][n + 1], a[blk][n + 2], a[blk][n + 3]);
+            zrow[(size_t)(n / 4) * Mp] = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
         }
         if (have_w) {
           if (p.w && real)
 #pragma unroll
             for (int n = 0; n < 32; n += 4)
               *reinterpret_cast<float4*>(p.w + o + n) =
-                  make_float4(a[blk][n], a[blk][n + 1], a[blk][n + 2], a[blk][n + 3]);
+                  make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
           if (p.w2out && real)  // refinement state (s o w, 0) as float pairs
 #pragma unroll
             for (int n = 0; n < 32; n += 2)
-              *reinterpret_cast<float4*>(p.w2out + o + n) = make_float4(sj * a[blk][n], 0.0f, sj * a[blk][n + 1], 0.0f);
+              *reinterpret_cast<float4*>(p.w2out + o + n) = make_float4(sj * a[n], 0.0f, sj * a[n + 1], 0.0f);
 #pragma unroll
-          for (int n = 0; n < 32; ++n) a[blk][n] *= hj;
-          dots[blk] = transpose_sum32(a[blk], lane);
+          for (int n = 0; n < 32; ++n) a[n] *= hj;
+          dots[blk] = transpose_sum32(a, lane);
         }
       }
       if (have_w)

@@ -82,7 +82,7 @@ def test_xbar64_rsweep_against_oracle(r_wire, precision, bar):
 # ragged shapes and edge cases
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("M,N,B", [(1, 1, 1), (1, 7, 5), (9, 1, 3), (5, 7, 37), (17, 33, 19), (33, 17, 200),
-                                   (40, 3, 1000), (3, 40, 9), (100, 20, 65)])
+                                   (40, 3, 1000), (3, 40, 9), (100, 20, 65), (513, 4, 33)])
 @pytest.mark.parametrize("precision,bar", [("fp64", FP64_BAR), ("fp32_ir", MIXED_BAR)])
 def test_ragged_shapes(M, N, B, precision, bar):
     G, V = case(M, N, B, None, seed=M * 1000 + N)
