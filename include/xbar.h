@@ -150,12 +150,22 @@ typedef enum {
                                  M <= 256).  Takes effect at the next xbar_factor. */
   XBAR_OPT_CR_PRODUCTS = 3,   /* cyclic reduction in XBAR_FP32_IR: 0 = products on the CUDA
                                  cores, 1 = on the tensor cores (three-term BF16 split; M >= 128) */
-  XBAR_OPT_WAIT_LIMIT_NS = 4  /* limit of every bounded device-side wait of this handle's
+  XBAR_OPT_WAIT_LIMIT_NS = 4, /* limit of every bounded device-side wait of this handle's
                                  kernels, in ns (value > 0); -1 or 0 restores the default of 2 s.
                                  A wait that runs out makes its kernel record a timeout and
                                  return; the next call that reads the handle's device status
                                  returns XBAR_ETIMEOUT and the results of that work are invalid.
                                  Synchronises the handle's stream. */
+  XBAR_OPT_ORIENTATION = 5    /* XBAR_FP64 factors: 0 = blocks over the N columns (M x M blocks,
+                                 bit lines eliminated inside each column; Sec. II-B ordering),
+                                 1 = blocks over the M rows (N x N blocks, word lines eliminated
+                                 inside each row: the same system written for the mirrored
+                                 crossbar M' = N, N' = M with R_s and R_sense, R_w and R_b
+                                 exchanged; needs N <= 1024), -1 (default) = rows when 2N <= M.
+                                 Results are the same up to rounding; the cost of the factor
+                                 scales as N M^3 or M N^3 and of a substitution as N M^2 or M N^2.
+                                 XBAR_FP32_IR factors always block over the columns.  Takes effect
+                                 at the next xbar_factor. */
 } xbar_option;
 
 /* Select a kernel variant for later xbar_factor / xbar_solve calls (value -1, 0 or 1; a

@@ -89,33 +89,12 @@ static xbar_status check_status(xbar_t h) {
   return XBAR_OK;
 }
 
-extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, double R_w, double R_b,
-                                     double R_sense, void* cuda_stream, xbar_t* out) {
-  if (!out) return fail(XBAR_EINVAL, "out is NULL");
+// A handle with every per-map array and its status block allocated; the map itself is stored by
+// the caller.  On failure nothing is left allocated.
+static xbar_status new_handle(int M, int N, const double R[4], cudaStream_t st, xbar_s** out) {
   *out = nullptr;
-  if (M < 1 || M > 1024) return fail(XBAR_EINVAL, "M=%d outside [1, 1024]", M);
-  if (N < 1 || N > (1 << 20)) return fail(XBAR_EINVAL, "N=%d outside [1, 2^20]", N);
-  if (!G) return fail(XBAR_EINVAL, "G is NULL");
-  const double R[4] = {R_s, R_w, R_b, R_sense};
-  const char* names[4] = {"R_s", "R_w", "R_b", "R_sense"};
-  for (int k = 0; k < 4; ++k)
-    if (!(R[k] > 0.0) || !isfinite(R[k])) return fail(XBAR_EINVAL, "%s=%g must be finite and > 0", names[k], R[k]);
-
-  // validate G on the host
-  std::vector<double> Gh((size_t)M * N);
-  const bool gdev = is_device_ptr(G);
-  if (gdev) {
-    cudaError_t e = cudaMemcpy(Gh.data(), G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(XBAR_ECUDA, "copy of G: %s", cudaGetErrorString(e));
-  } else {
-    memcpy(Gh.data(), G, Gh.size() * sizeof(double));
-  }
-  for (size_t k = 0; k < Gh.size(); ++k)
-    if (!(Gh[k] >= 0.0) || !isfinite(Gh[k]))
-      return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, Gh[k]);
-
   xbar_s* h = new xbar_s();
-  h->st = (cudaStream_t)cuda_stream;
+  h->st = st;
   for (int k = 0; k < 4; ++k) h->R[k] = R[k];
   cudaGetDevice(&h->dev);
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
@@ -123,10 +102,10 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   m.M = M;
   m.N = N;
   m.Mp = round_up(M, 16);
-  m.gs = 1.0 / R_s;
-  m.gw = 1.0 / R_w;
-  m.gb = 1.0 / R_b;
-  m.go = 1.0 / R_sense;
+  m.gs = 1.0 / R[0];
+  m.gw = 1.0 / R[1];
+  m.gb = 1.0 / R[2];
+  m.go = 1.0 / R[3];
   const size_t nv = (size_t)N * m.Mp;
   auto cleanup = [&](xbar_status s) {
     h->A.free_all();
@@ -164,12 +143,59 @@ extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, 
   XB_ALLOC(m.tha2, nv * 8);
   XB_ALLOC(m.thc2, nv * 8);
   XB_ALLOC(h->status, sizeof(DevStatus));
+  cudaError_t e0 = cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->st);  // no bits, default wait limit
+  if (e0 != cudaSuccess) return cleanup(fail(XBAR_ECUDA, "status block: %s", cudaGetErrorString(e0)));
+#undef XB_ALLOC
+  *out = h;
+  return XBAR_OK;
+}
+
+extern "C" xbar_status xbar_assemble(int M, int N, const double* G, double R_s, double R_w, double R_b,
+                                     double R_sense, void* cuda_stream, xbar_t* out) {
+  if (!out) return fail(XBAR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (M < 1 || M > 1024) return fail(XBAR_EINVAL, "M=%d outside [1, 1024]", M);
+  if (N < 1 || N > (1 << 20)) return fail(XBAR_EINVAL, "N=%d outside [1, 2^20]", N);
+  if (!G) return fail(XBAR_EINVAL, "G is NULL");
+  const double R[4] = {R_s, R_w, R_b, R_sense};
+  const char* names[4] = {"R_s", "R_w", "R_b", "R_sense"};
+  for (int k = 0; k < 4; ++k)
+    if (!(R[k] > 0.0) || !isfinite(R[k])) return fail(XBAR_EINVAL, "%s=%g must be finite and > 0", names[k], R[k]);
+
+  // validate G on the host
+  std::vector<double> Gh((size_t)M * N);
+  const bool gdev = is_device_ptr(G);
+  if (gdev) {
+    cudaError_t e = cudaMemcpy(Gh.data(), G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(XBAR_ECUDA, "copy of G: %s", cudaGetErrorString(e));
+  } else {
+    memcpy(Gh.data(), G, Gh.size() * sizeof(double));
+  }
+  for (size_t k = 0; k < Gh.size(); ++k)
+    if (!(Gh[k] >= 0.0) || !isfinite(Gh[k]))
+      return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, Gh[k]);
+
+  xbar_s* h = nullptr;
+  xbar_status hs = new_handle(M, N, R, (cudaStream_t)cuda_stream, &h);
+  if (hs != XBAR_OK) return hs;
+  MapDev& m = h->m;
+  auto cleanup = [&](xbar_status s) {
+    h->A.free_all();
+    delete h;
+    return s;
+  };
+#define XB_ALLOC(ptr, bytes)                                                          \
+  do {                                                                                \
+    cudaError_t e_ = h->A.alloc((void**)&(ptr), (bytes));                             \
+    if (e_ != cudaSuccess) {                                                          \
+      cudaGetLastError();                                                             \
+      return cleanup(fail(XBAR_ENOMEM, "cudaMalloc(%zu): %s", (size_t)(bytes), cudaGetErrorString(e_))); \
+    }                                                                                 \
+  } while (0)
   double* Gd = nullptr;
   XB_ALLOC(Gd, (size_t)M * N * 8);
 #undef XB_ALLOC
-  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->st);  // no bits, default wait limit
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(Gd, Gh.data(), (size_t)M * N * 8, cudaMemcpyHostToDevice, h->st);
+  cudaError_t e = cudaMemcpyAsync(Gd, Gh.data(), (size_t)M * N * 8, cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess) {
     PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
     e = launch_store_g(m, Gd, nullptr, h->st);  // validated on the host above
@@ -193,8 +219,8 @@ static int cr_sweep_launches(const xbar_s* h, int B, bool initial) {
 // BF16 terms of the tensor-core sweep for refinement correction `it` (0-based).  A correction
 // only needs accuracy relative to its own size, so the first two are solved with two terms
 // (~2^-17 per product); one term (2^-9 per product, accumulated over the 2N - 1 dependent steps)
-// proved too coarse to certify convergence.  Any later correction (slow convergence) and the
-// initial solve use all three (FP32-level accuracy).
+// proved too coarse to certify convergence.  Any later correction (slow convergence) uses all
+// three (FP32-level accuracy).
 static int correction_terms(int it) { return it < 2 ? 2 : 3; }
 // The initial solve's error is set by the FP32 factor (~1e-4..1e-3 relative at 256 x 256), far
 // above what the two leading BF16 terms of the factor blocks add (~2^-17 per product): the third
@@ -238,6 +264,113 @@ static bool use_cr_tensor(const xbar_s* h) {
   if (e && strcmp(e, "simt") == 0) return false;
   if (e && strcmp(e, "tc") == 0) return true;
   return h->opt.cr_tensor != 0;
+}
+
+// Blocking over rows (orient.cu) for FP64 factors: the handle's option 1 (rows) or 0 (columns), or
+// XBAR_ORIENT=rows|columns; automatic (-1): rows when 2N <= M, where the N x N blocks make the
+// factor ~(M/N)^2 and each substitution ~M/N times cheaper.  The mirror has N rows per block, so
+// N must be within the handle limit of 1024.
+static bool use_rows(const xbar_s* h, xbar_precision p) {
+  if (p != XBAR_FP64 || h->m.N > 1024) return false;
+  const char* e = getenv("XBAR_ORIENT");
+  if (e && strcmp(e, "columns") == 0) return false;
+  if (e && strcmp(e, "rows") == 0) return true;
+  if (h->opt.orient >= 0) return h->opt.orient == 1;
+  return 2 * h->m.N <= h->m.M;
+}
+
+// Build (once) and refresh the mirrored crossbar from this handle's map, then factor it in FP64.
+// The mirror shares the handle's stream, device and status block.
+static xbar_status factor_mirror(xbar_s* h) {
+  const MapDev& m = h->m;
+  if (!h->mirror) {
+    // R_s' = R_sense, R_w' = R_b, R_b' = R_w, R_sense' = R_s
+    const double R2[4] = {h->R[3], h->R[2], h->R[1], h->R[0]};
+    xbar_s* g = nullptr;
+    xbar_status s = new_handle(m.N, m.M, R2, h->st, &g);
+    if (s != XBAR_OK) return s;
+    g->A.release(g->status);
+    g->status = h->status;
+    h->mirror = g;
+  }
+  xbar_s* g = h->mirror;
+  g->opt = h->opt;
+  g->opt.orient = 0;
+  g->prof_on = 0;  // the caller's phase scopes count the mirror's launches
+  XB_CUDA(launch_mirror_gc(m.Gc, m.M, m.Mp, m.N, g->m.Gc, g->m.Mp, h->st));
+  g->assembled = 0;
+  return factor_handle(g, XBAR_FP64, true);
+}
+
+// FP64 solve of a row-blocked factorization: the mirror's right-hand side, its substitution (block
+// Thomas or cyclic reduction, as it was factored), the currents from its first block and, if asked,
+// the node voltages mapped back.  Workspace in the mirror (grown only with allow_alloc).
+static xbar_status solve_rows(xbar_s* h, int B, const double* dV, double* dI, double* dvWL, double* dvBL,
+                              bool allow_alloc) {
+  xbar_s* g = h->mirror;
+  const MapDev& m2 = g->m;
+  const int M = h->m.M, N = h->m.N, M2 = m2.M, Mp2 = m2.Mp, N2 = m2.N;
+  cudaStream_t st = h->st;
+  const bool cr = g->cr_active != 0;
+  const int Bp = cr ? kCrPanel : sweep_panel_width<double>(Mp2, B, g->nsm);
+  const int Bpad = ((B + Bp - 1) / Bp) * Bp;
+  const size_t nst = (size_t)N2 * Mp2 * Bpad;
+  auto need = [&](Buf& b, size_t bytes) -> bool {
+    if (b.p && b.bytes >= bytes) return true;
+    return allow_alloc && ensure(g->A, b, bytes) == cudaSuccess;
+  };
+  if (!need(g->z, nst * 8) || !need(g->w64, nst * 8) || !need(g->phi, nst * 8) ||
+      !need(g->sI, (size_t)Bpad * N2 * 8))
+    return fail(XBAR_ENOMEM, "workspace of the row-blocked solve");
+  double* rhs = (double*)g->phi.p;  // consumed by the substitution; then the mirror's bit-line voltages
+  double* w2 = (double*)g->w64.p;
+  {
+    PhaseScope ps(h, XBAR_PHASE_SWEEP, 2 + (cr ? cr_sweep_launches(g, B, false) : 1));
+    XB_CUDA(launch_orient_rhs(dV, m2.h, M, M2, Mp2, B, Bpad, rhs, st));
+    if (cr) {
+      CrSweepArgs<double> ca;
+      memset(&ca, 0, sizeof(ca));
+      ca.B = B;
+      ca.Bpad = Bpad;
+      ca.V = nullptr;
+      ca.src = m2.src_pl;
+      ca.r = rhs;
+      ca.x = w2;
+      ca.e = m2.e_pl;
+      ca.hs = m2.h;
+      ca.I = (double*)g->sI.p;
+      XB_CUDA(cr_sweep<double>(g, g->cr64, ca));
+    } else {
+      SweepParams<double> sp;
+      sp.M = M2;
+      sp.Mp = Mp2;
+      sp.N = N2;
+      sp.B = B;
+      sp.Bp = Bp;
+      sp.Bpad = Bpad;
+      sp.X = (const double*)g->X.p;
+      sp.e = m2.e_pl;
+      sp.hs = m2.h;
+      sp.src = m2.src_pl;
+      sp.V = nullptr;
+      sp.rhs = rhs;
+      sp.z = (double*)g->z.p;
+      sp.w = w2;
+      sp.I = (double*)g->sI.p;
+      sp.accumulate = 0;
+      sp.max_rel = nullptr;
+      sp.status = g->status;
+      XB_CUDA(launch_sweep<double>(sp, st));
+    }
+    XB_CUDA(launch_orient_currents(w2, N, Bpad, B, m2.gs, dI, st));
+  }
+  if (dvWL || dvBL) {
+    PhaseScope ps(h, XBAR_PHASE_OUTPUT, 1 + (dvWL ? 1 : 0) + (dvBL ? 1 : 0));
+    XB_CUDA(launch_orient_blvolt(m2, w2, dV, M, B, Bpad, rhs, st));
+    if (dvWL) XB_CUDA(launch_orient_to_user(rhs, dvWL, M, N, Mp2, B, Bpad, st));  // original WL = mirror BL
+    if (dvBL) XB_CUDA(launch_orient_to_user(w2, dvBL, M, N, Mp2, B, Bpad, st));   // original BL = mirror WL
+  }
+  return XBAR_OK;
 }
 
 template <typename T>
@@ -316,6 +449,20 @@ static xbar_status do_factor(xbar_t h, bool equilibrate, bool upload) {
 xbar_status xbar::factor_handle(xbar_s* h, xbar_precision p, bool upload_params) {
   h->factored = 0;
   h->geff_valid = 0;
+  h->orient_active = 0;
+  if (use_rows(h, p)) {  // the mirrored crossbar (blocks over rows), factored in this handle's place
+    PhaseScope ps(h, XBAR_PHASE_FACTOR, 1);
+    xbar_status s = factor_mirror(h);
+    if (s != XBAR_OK) return s;
+    // map remap + assembly (3) + the factor (one launch, or the cyclic reduction's operations)
+    ps.nlaunch = 4 + (h->mirror->cr_active ? (int)h->mirror->cr64.ops.size() : 1);
+    h->orient_active = 1;
+    h->cr_active = 0;
+    h->tc_ready = 0;
+    h->prec = p;
+    h->factored = 1;
+    return XBAR_OK;
+  }
   if (!h->assembled) {  // the elimination data of the current conductances
     PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 3);
     XB_CUDA(launch_assemble(h->m, h->st));
@@ -359,6 +506,7 @@ extern "C" xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value) {
     case XBAR_OPT_FACTOR_KERNEL: h->opt.factor = value; break;
     case XBAR_OPT_ALGORITHM: h->opt.algo = value; break;
     case XBAR_OPT_CR_PRODUCTS: h->opt.cr_tensor = value; break;
+    case XBAR_OPT_ORIENTATION: h->opt.orient = value; break;
     default: return fail(XBAR_EINVAL, "unknown option %d", (int)opt);
   }
   return XBAR_OK;
@@ -411,6 +559,19 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
   if (vBL && !bdev) {
     XB_CUDA(ensure(h->A, h->svBL, nvolt * 8));
     dvBL = (double*)h->svBL.p;
+  }
+
+  if (h->orient_active) {  // FP64, blocked over rows: the mirrored crossbar's solve
+    xbar_status s = solve_rows(h, B, dV, dI, dvWL, dvBL, true);
+    if (s != XBAR_OK) return s;
+    if (!idev) XB_CUDA(cudaMemcpyAsync(I, dI, nIB * 8, cudaMemcpyDeviceToHost, st));
+    if (vWL && !wdev) XB_CUDA(cudaMemcpyAsync(vWL, dvWL, nvolt * 8, cudaMemcpyDeviceToHost, st));
+    if (vBL && !bdev) XB_CUDA(cudaMemcpyAsync(vBL, dvBL, nvolt * 8, cudaMemcpyDeviceToHost, st));
+    if (!idev || (vWL && !wdev) || (vBL && !bdev) || !vdev) {
+      xbar_status cs = check_status(h);
+      if (cs != XBAR_OK) return cs;
+    }
+    return XBAR_OK;  // info: zeros (no refinement)
   }
 
   const bool cr = h->cr_active != 0;
@@ -650,6 +811,13 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   MapDev& m = h->m;
   const int M = m.M, Mp = m.Mp, N = m.N;
   cudaStream_t st = h->st;
+  if (h->orient_active) {  // FP64, blocked over rows (stream-ordered launches only)
+    if (!(h->irstate.p && h->irstate.bytes >= sizeof(IrState)) &&
+        !(allow_alloc && ensure(h->A, h->irstate, sizeof(IrState)) == cudaSuccess))
+      return fail(XBAR_ENOMEM, "refinement state");
+    XB_CUDA(launch_ir_init((IrState*)h->irstate.p, st));
+    return solve_rows(h, B, dV, dI, nullptr, nullptr, allow_alloc);
+  }
   if (h->cr_active)
     return fail(XBAR_ESTATE, "device-driven solves (tile batches) need a block-Thomas factorization");
   const bool mixed = h->prec == XBAR_FP32_IR;
@@ -726,6 +894,10 @@ extern "C" xbar_status xbar_destroy(xbar_t h) {
   if (!h) return XBAR_OK;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->st);
+  if (h->mirror) {  // its status block is this handle's: not in its arena
+    xbar_destroy(h->mirror);
+    h->mirror = nullptr;
+  }
   for (auto& pe : h->pending) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
@@ -897,8 +1069,9 @@ extern "C" xbar_status xbar_solve_transfer(xbar_t h, int B, const double* V, dou
 
 extern "C" xbar_status xbar_solve_noalloc(xbar_t h, int B, const double* V, double* I) {
   if (!h) return fail(XBAR_EINVAL, "handle is NULL");
-  if (!h->factored || h->prec != XBAR_FP64 || h->cr_active)
-    return fail(XBAR_ESTATE, "xbar_solve_noalloc needs a handle factored with XBAR_FP64 by block Thomas");
+  if (!h->factored || h->prec != XBAR_FP64 || h->cr_active || h->orient_active)
+    return fail(XBAR_ESTATE,
+                "xbar_solve_noalloc needs a handle factored with XBAR_FP64 by block Thomas over columns");
   if (B < 0) return fail(XBAR_EINVAL, "B=%d < 0", B);
   if (B == 0) return XBAR_OK;
   if (!V || !I) return fail(XBAR_EINVAL, "V and I must not be NULL");

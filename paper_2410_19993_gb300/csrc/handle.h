@@ -96,6 +96,7 @@ struct xbar_opts {
   int factor = -1;  // 0 = cooperative-group factor, 1 = cluster factor
   int algo = -1;    // 0 = block Thomas, 1 = block cyclic reduction
   int cr_tensor = -1;  // cyclic reduction, FP32 products: 0 = CUDA cores, 1 = tensor cores
+  int orient = -1;  // FP64 factors: 0 = column blocks, 1 = row blocks (mirrored crossbar), -1 = rows when 2N <= M
 };
 
 struct xbar_s {
@@ -126,6 +127,10 @@ struct xbar_s {
   xbar::CrPlan<float> cr32;
   xbar::CrPlan<double> cr64;
   int cr_active = 0;
+  // blocking over rows (orient.cu): the mirrored crossbar, factored in this handle's place when
+  // orient_active (FP64 factors only); it shares this handle's stream and device
+  xbar_s* mirror = nullptr;
+  int orient_active = 0;
   // transfer-matrix mode: G_eff of the current factorization (valid until the next factor)
   xbar::Buf geff, eye;
   int geff_valid = 0;

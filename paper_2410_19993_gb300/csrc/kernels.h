@@ -117,6 +117,22 @@ cudaError_t launch_sweep_tc_tile(const float* X, void* Xt, int Mp, int N, cudaSt
 // terms = leading BF16 terms of the split used (1..3): 3 gives FP32-level accuracy
 cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, int terms, cudaStream_t st);
 
+// ---- blocking over rows (orient.cu): the mirrored crossbar M' = N, N' = M ---------------------
+// Gc2[j'][i'] = Gc[N-1-i'][M-1-j'] (Gc: [N][Mp] of the original, Gc2: [M][Mp2], Mp2 >= N)
+cudaError_t launch_mirror_gc(const double* Gc, int M, int Mp, int N, double* Gc2, int Mp2, cudaStream_t st);
+// rhs[j'][i'][b] = V[b][M-1-j'] h2[j'][i'] ([M][Mp2][Bpad]; zero in padding rows and vectors)
+cudaError_t launch_orient_rhs(const double* V, const double* h2, int M, int M2, int Mp2, int B, int Bpad,
+                              double* rhs, cudaStream_t st);
+// I[b][j] = gs2 w2[0][N-1-j][b]
+cudaError_t launch_orient_currents(const double* w2, int N, int Bpad, int B, double gs2, double* I,
+                                   cudaStream_t st);
+// the mirror's bit-line voltages u ([M][Mp2][Bpad]) from its word-line voltages w2 and the sources
+cudaError_t launch_orient_blvolt(const MapDev& m2, const double* w2, const double* V, int M, int B, int Bpad,
+                                 double* u, cudaStream_t st);
+// out[b][i][j] = src2[M-1-i][N-1-j][b]
+cudaError_t launch_orient_to_user(const double* src2, double* out, int M, int N, int Mp2, int B, int Bpad,
+                                  cudaStream_t st);
+
 // ---- transfer-matrix mode (transfer.cu) -------------------------------------------------------
 cudaError_t launch_eye(double* E, int M, cudaStream_t st);  // E = I (M x M, FP64)
 // C[R x N] = A[R x K] . B[K x N], FP64, row-major

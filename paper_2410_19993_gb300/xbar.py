@@ -51,8 +51,11 @@ class TileDesc(ctypes.Structure):
                 ("R_w", ctypes.c_double), ("R_b", ctypes.c_double), ("R_sense", ctypes.c_double)]
 
 
-OPTIONS = {"sweep_kernel": 0, "factor_kernel": 1, "algorithm": 2, "cr_products": 3, "wait_limit_ns": 4}
+OPTIONS = {"sweep_kernel": 0, "factor_kernel": 1, "algorithm": 2, "cr_products": 3, "wait_limit_ns": 4,
+           "orientation": 5}
 ALGORITHMS = {"thomas": 0, "cr": 1}
+ORIENTATIONS = {"auto": -1, "columns": 0, "rows": 1}
+_VALUE_NAMES = {"algorithm": ALGORITHMS, "orientation": ORIENTATIONS}
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -256,8 +259,9 @@ class Crossbar:
 
     def set_option(self, name, value):
         """xbar_set_option: 'sweep_kernel' (0 CUDA cores, 1 tensor cores) / 'factor_kernel' (0 group,
-        1 cluster) / 'algorithm' (0 or 'thomas', 1 or 'cr') / 'cr_products' (0 CUDA cores, 1 tensor cores)."""
-        value = ALGORITHMS.get(value, value)
+        1 cluster) / 'algorithm' (0 or 'thomas', 1 or 'cr') / 'cr_products' (0 CUDA cores, 1 tensor cores)
+        / 'wait_limit_ns' / 'orientation' (-1 or 'auto', 0 or 'columns', 1 or 'rows'; FP64 factors)."""
+        value = _VALUE_NAMES.get(name, {}).get(value, value)
         _check(load().xbar_set_option(self.handle, OPTIONS[name], int(value)))
         return self
 
