@@ -10,8 +10,9 @@
 // Later runs with the same signature replay the instantiated graph with a single cudaGraphLaunch.
 //
 // The autotuner times the kernel variants (tensor-core vs CUDA-core FP32 substitutions, cluster
-// vs cooperative-group FP32 factor) on one tile of every distinct (M, N, B), keeps the fastest,
-// and can persist its choices in a small JSON file keyed by shape.
+// vs cooperative-group FP32 factor; for FP64, blocks over columns vs over rows -- the mirrored
+// crossbar of orient.cu) on one tile of every distinct (M, N, B), keeps the fastest, and can
+// persist its choices in a small JSON file keyed by shape.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -235,8 +236,9 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int sweep = -1, factor = -1;
+  int sweep = -1, factor = -1, orient = -1;
   float sweep_ms[2] = {-1, -1}, factor_ms[2] = {-1, -1};
+  float orient_ms[2] = {-1, -1};  // FP64: factor + solve, blocks over columns / rows
 };
 
 static std::string key_str(const TuneKey& k) {
@@ -254,9 +256,9 @@ static std::map<TuneKey, TuneVal> load_cache(const char* path) {
   while (fgets(line, sizeof(line), f)) {
     TuneKey k;
     TuneVal v;
-    if (sscanf(line, " \"M=%d,N=%d,B=%d,prec=%d\": {\"sweep\": %d, \"factor\": %d", &k.M, &k.N, &k.B, &k.p,
-               &v.sweep, &v.factor) == 6)
-      c[k] = v;
+    const int n = sscanf(line, " \"M=%d,N=%d,B=%d,prec=%d\": {\"sweep\": %d, \"factor\": %d, \"orient\": %d", &k.M,
+                         &k.N, &k.B, &k.p, &v.sweep, &v.factor, &v.orient);
+    if (n >= 6) c[k] = v;  // files written before the orientation field: automatic orientation
   }
   fclose(f);
   return c;
@@ -271,9 +273,10 @@ static void save_cache(const char* path, const std::map<TuneKey, TuneVal>& c) {
   for (const auto& kv : c) {
     const TuneVal& v = kv.second;
     fprintf(f,
-            "  \"%s\": {\"sweep\": %d, \"factor\": %d, \"sweep_ms\": [%.4f, %.4f], \"factor_ms\": [%.4f, %.4f]}%s\n",
-            key_str(kv.first).c_str(), v.sweep, v.factor, v.sweep_ms[0], v.sweep_ms[1], v.factor_ms[0],
-            v.factor_ms[1], ++n < c.size() ? "," : "");
+            "  \"%s\": {\"sweep\": %d, \"factor\": %d, \"orient\": %d, \"sweep_ms\": [%.4f, %.4f], "
+            "\"factor_ms\": [%.4f, %.4f], \"orient_ms\": [%.4f, %.4f]}%s\n",
+            key_str(kv.first).c_str(), v.sweep, v.factor, v.orient, v.sweep_ms[0], v.sweep_ms[1], v.factor_ms[0],
+            v.factor_ms[1], v.orient_ms[0], v.orient_ms[1], ++n < c.size() ? "," : "");
   }
   fprintf(f, "}\n");
   fclose(f);
@@ -344,6 +347,28 @@ extern "C" xbar_status xbar_batch_autotune(xbar_batch_t b, xbar_precision p, con
       cudaFree(dI);
       cache[k] = v;
       changed = true;
+    } else if (p == XBAR_FP64 && k.B > 0) {
+      // FP64: blocks over columns vs over rows, each timed as factor + device-driven solve
+      double *dV = nullptr, *dI = nullptr;
+      XB_CUDA(cudaMalloc(&dV, (size_t)k.B * k.M * 8));
+      XB_CUDA(cudaMalloc(&dI, (size_t)k.B * k.N * 8));
+      std::vector<double> hv((size_t)k.B * k.M, 0.25);
+      cudaMemcpy(dV, hv.data(), hv.size() * 8, cudaMemcpyHostToDevice);
+      const int save_o = h->opt.orient;
+      for (int o = 0; o < 2; ++o) {
+        if (o == 1 && k.N > 1024) continue;
+        h->opt.orient = o;
+        v.orient_ms[o] = time_ms(h->st, [&]() {
+          xbar_status s = factor_handle(h, p, true);
+          return s != XBAR_OK ? s : solve_device_driven(h, k.B, dV, dI, 1e-8, 0, true);
+        });
+      }
+      v.orient = (v.orient_ms[1] >= 0 && (v.orient_ms[0] < 0 || v.orient_ms[1] < v.orient_ms[0])) ? 1 : 0;
+      h->opt.orient = save_o;
+      cudaFree(dV);
+      cudaFree(dI);
+      cache[k] = v;
+      changed = true;
     }
     // apply to every tile of this shape
     for (int t = 0; t < b->T; ++t) {
@@ -351,6 +376,7 @@ extern "C" xbar_status xbar_batch_autotune(xbar_batch_t b, xbar_precision p, con
       if (ht->m.M == k.M && ht->m.N == k.N && B[t] == k.B) {
         ht->opt.sweep = v.sweep;
         ht->opt.factor = v.factor;
+        if (p == XBAR_FP64) ht->opt.orient = v.orient;
       }
     }
   }

@@ -28,6 +28,13 @@ def oracle_transfer(M, N, R, seed=0):
     return oracle.transfer_matrix(f)
 
 
+def oracle_transfer_of(args):
+    """The oracle's transfer matrix of one (G, R) pair (a process-pool worker: numpy and the oracle
+    only)."""
+    G, R = args
+    return oracle.transfer_matrix(oracle.factor(G.shape[0], G.shape[1], G, *R))
+
+
 def case(M, N, B, R, seed=0, v_max=0.5):
     """(G, V) drawn with the workload recipe; G first, then V (same stream as inputs.crossbar)."""
     return inputs.crossbar(M, N, B, seed, v_max=v_max)

@@ -2,16 +2,18 @@
 
 Every tile of a batch run is compared with the single-crossbar path of the same library (itself
 checked against the oracle in test_gpu_parity.py), and one tile of each distinct shape directly
-with the CPU oracle's transfer matrix.
+with the CPU oracle's transfer matrix; at the workload's full size (4096 vectors per tile) every
+tile is compared with the oracle's transfer matrix.
 """
 import json
+import multiprocessing
 
 import numpy as np
 import pytest
 
 import oracle
 from paper_2410_19993_gb300 import inputs, xbar
-from tests.gpu_common import rel_err
+from tests.gpu_common import oracle_transfer_of, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -108,6 +110,54 @@ def test_autotune_cache(tiles, tmp_path):
     b2.destroy()
     for a, c in zip(out, out2):
         assert rel_err(c, a) <= 1e-8
+
+
+@pytest.fixture(scope="module")
+def full_tiles():
+    """The 30 tiles with 4096 vectors each and the oracle's transfer matrix of every tile (CPU, in
+    a spawned process pool: a pool forked after CUDA initialisation can hang)."""
+    ts = inputs.fc_tiles(B=4096)
+    with multiprocessing.get_context("spawn").Pool(min(8, multiprocessing.cpu_count())) as pool:
+        T = pool.map(oracle_transfer_of, [(t.G, t.circuit.as_tuple()) for t in ts])
+    return ts, T
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32_ir", 1e-8)])
+def test_batch_full_size_every_tile_against_oracle(full_tiles, precision, bar):
+    ts, T = full_tiles
+    b = _batch(ts)
+    out, infos = _run(b, ts, precision)
+    b.destroy()
+    for t, I, Geff, info in zip(ts, out, T, infos):
+        assert rel_err(I, t.V @ Geff) <= bar, t.G.shape
+        if precision == "fp32_ir":
+            assert 1 <= info["iters"] <= 6
+
+
+def test_autotune_fp64_orientation(tiles, tmp_path):
+    """FP64 autotuning times blocks over columns and over rows per shape; whatever it picks, the
+    currents stay those of the single path."""
+    path = str(tmp_path / "tune64.json")
+    b = _batch(tiles)
+    B = [t.V.shape[0] for t in tiles]
+    b.autotune("fp64", B, path)
+    data = json.load(open(path))
+    assert len(data) == 3
+    for v in data.values():
+        assert v["orient"] in (0, 1)
+        assert v["orient_ms"][0] > 0  # columns always timed
+    out, _ = _run(b, tiles, "fp64")
+    b.destroy()
+    for t, I in zip(tiles, out):
+        xb = xbar.Crossbar.assemble(_dev(t.G), *t.circuit.as_tuple())
+        xb.set_option("orientation", "columns")
+        xb.factor("fp64")
+        Iref = torch.zeros_like(torch.from_numpy(I)).cuda()
+        xb.solve(_dev(t.V), Iref)
+        xb.sync()
+        assert rel_err(I, Iref.cpu().numpy()) <= 1e-11
+        xb.destroy()
 
 
 def test_batch_rejects_host_buffers(tiles):
