@@ -604,7 +604,10 @@ def run_paper_experiments(args):
     solve split for batches of 1, 2, 10, 100 and 1000.  Parasitic resistors 5 Ohm each (source and
     sense resistors equal to the wire segments), random conductances and voltages as elsewhere.
     Each time is the wall time of the user-visible calls with the stream synchronised, mean of 10
-    runs; the FP64 path is the paper's method (LU in FP64), the mixed path is given beside it."""
+    runs; the FP64 path is the paper's method (LU in FP64), the mixed path is given beside it.  Each
+    single-map case runs with the handle's default algorithm (block Thomas; blocks over rows, and
+    there cyclic reduction, when 2n <= m in FP64) and again with block cyclic reduction over the
+    blocks ('_cr' keys)."""
     import torch
 
     from paper_2410_19993_gb300 import inputs, xbar
@@ -632,12 +635,14 @@ def run_paper_experiments(args):
             I = torch.zeros((1, n), dtype=torch.float64, device="cuda")
             xb = xbar.Crossbar.assemble(Gd, *R)
             row = {"m": m, "n": n}
-            for prec in ("fp64", "fp32_ir"):
-                def sim():
-                    xb.set_conductances(Gd)
-                    xb.factor(prec)
-                    xb.solve(Vd, I, tol=TOL, max_iter=10)
-                row[prec + "_ms"] = wall(sim)
+            for algo in ("auto", "cr"):
+                xb.set_option("algorithm", -1 if algo == "auto" else "cr")
+                for prec in ("fp64", "fp32_ir"):
+                    def sim():
+                        xb.set_conductances(Gd)
+                        xb.factor(prec)
+                        xb.solve(Vd, I, tol=TOL, max_iter=10)
+                    row[prec + ("_cr" if algo == "cr" else "") + "_ms"] = wall(sim)
             xb.destroy()
             size_sweep.append(row)
 
@@ -668,14 +673,17 @@ def run_paper_experiments(args):
             I = torch.zeros((B, m), dtype=torch.float64, device="cuda")
             xb = xbar.Crossbar.assemble(Gd, *R)
             row = {"m": m, "n": m, "B": B}
-            for prec in ("fp64", "fp32_ir"):
-                def dec():
-                    xb.set_conductances(Gd)
-                    xb.factor(prec)
-                t_dec = wall(dec)
-                t_sol = wall(lambda: xb.solve(Vd, I, tol=TOL, max_iter=10))
-                row[prec] = {"decompose_ms": t_dec, "solve_ms": t_sol, "solve_share": t_sol / (t_dec + t_sol),
-                             "per_sample_ms": (t_dec + t_sol) / B}
+            for algo in ("auto", "cr"):
+                xb.set_option("algorithm", -1 if algo == "auto" else "cr")
+                for prec in ("fp64", "fp32_ir"):
+                    def dec():
+                        xb.set_conductances(Gd)
+                        xb.factor(prec)
+                    t_dec = wall(dec)
+                    t_sol = wall(lambda: xb.solve(Vd, I, tol=TOL, max_iter=10))
+                    row[prec + ("_cr" if algo == "cr" else "")] = {
+                        "decompose_ms": t_dec, "solve_ms": t_sol, "solve_share": t_sol / (t_dec + t_sol),
+                        "per_sample_ms": (t_dec + t_sol) / B}
             xb.destroy()
             split.append(row)
 

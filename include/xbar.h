@@ -162,6 +162,9 @@ typedef enum {
                                  inside each row: the same system written for the mirrored
                                  crossbar M' = N, N' = M with R_s and R_sense, R_w and R_b
                                  exchanged; needs N <= 1024), -1 (default) = rows when 2N <= M.
+                                 Blocked over rows with XBAR_OPT_ALGORITHM left at -1, the factor
+                                 is block cyclic reduction when N <= 256 (its M small blocks are
+                                 what cyclic reduction is for), else block Thomas.
                                  Results are the same up to rounding; the cost of the factor
                                  scales as N M^3 or M N^3 and of a substitution as N M^2 or M N^2.
                                  XBAR_FP32_IR factors always block over the columns.  Takes effect

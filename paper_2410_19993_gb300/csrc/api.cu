@@ -296,6 +296,9 @@ static xbar_status factor_mirror(xbar_s* h) {
   xbar_s* g = h->mirror;
   g->opt = h->opt;
   g->opt.orient = 0;
+  // automatic algorithm: the mirror's many small blocks (M blocks of N rows) are what cyclic
+  // reduction is for, against M dependent block steps of block Thomas
+  if (h->opt.algo < 0 && cr_supported(g->m.Mp, g->m.N)) g->opt.algo = 1;
   g->prof_on = 0;  // the caller's phase scopes count the mirror's launches
   XB_CUDA(launch_mirror_gc(m.Gc, m.M, m.Mp, m.N, g->m.Gc, g->m.Mp, h->st));
   g->assembled = 0;
