@@ -167,8 +167,10 @@ typedef enum {
                                  what cyclic reduction is for), else block Thomas.
                                  Results are the same up to rounding; the cost of the factor
                                  scales as N M^3 or M N^3 and of a substitution as N M^2 or M N^2.
-                                 XBAR_FP32_IR factors always block over the columns.  Takes effect
-                                 at the next xbar_factor. */
+                                 XBAR_FP32_IR factors block over rows only when this option is 1
+                                 (the refinement then runs on the mirrored crossbar); the tile
+                                 batch (xbar_batch_run) blocks over rows in XBAR_FP64 only.  Takes
+                                 effect at the next xbar_factor. */
 } xbar_option;
 
 /* Select a kernel variant for later xbar_factor / xbar_solve calls (value -1, 0 or 1; a

@@ -266,22 +266,22 @@ static bool use_cr_tensor(const xbar_s* h) {
   return h->opt.cr_tensor != 0;
 }
 
-// Blocking over rows (orient.cu) for FP64 factors: the handle's option 1 (rows) or 0 (columns), or
-// XBAR_ORIENT=rows|columns; automatic (-1): rows when 2N <= M, where the N x N blocks make the
-// factor ~(M/N)^2 and each substitution ~M/N times cheaper.  The mirror has N rows per block, so
-// N must be within the handle limit of 1024.
+// Blocking over rows (orient.cu): the handle's option 1 (rows) or 0 (columns), or
+// XBAR_ORIENT=rows|columns; automatic (-1): rows for FP64 factors when 2N <= M, where the N x N
+// blocks make the factor ~(M/N)^2 and each substitution ~M/N times cheaper (mixed precision keeps
+// columns unless asked).  The mirror has N rows per block, so N must be within the handle limit.
 static bool use_rows(const xbar_s* h, xbar_precision p) {
-  if (p != XBAR_FP64 || h->m.N > 1024) return false;
+  if (h->m.N > 1024) return false;
   const char* e = getenv("XBAR_ORIENT");
   if (e && strcmp(e, "columns") == 0) return false;
   if (e && strcmp(e, "rows") == 0) return true;
   if (h->opt.orient >= 0) return h->opt.orient == 1;
-  return 2 * h->m.N <= h->m.M;
+  return p == XBAR_FP64 && 2 * h->m.N <= h->m.M;
 }
 
-// Build (once) and refresh the mirrored crossbar from this handle's map, then factor it in FP64.
-// The mirror shares the handle's stream, device and status block.
-static xbar_status factor_mirror(xbar_s* h) {
+// Build (once) and refresh the mirrored crossbar from this handle's map, then factor it in
+// precision p.  The mirror shares the handle's stream, device and status block.
+static xbar_status factor_mirror(xbar_s* h, xbar_precision p) {
   const MapDev& m = h->m;
   if (!h->mirror) {
     // R_s' = R_sense, R_w' = R_b, R_b' = R_w, R_sense' = R_s
@@ -302,7 +302,7 @@ static xbar_status factor_mirror(xbar_s* h) {
   g->prof_on = 0;  // the caller's phase scopes count the mirror's launches
   XB_CUDA(launch_mirror_gc(m.Gc, m.M, m.Mp, m.N, g->m.Gc, g->m.Mp, h->st));
   g->assembled = 0;
-  return factor_handle(g, XBAR_FP64, true);
+  return factor_handle(g, p, true);
 }
 
 // FP64 solve of a row-blocked factorization: the mirror's right-hand side, its substitution (block
@@ -372,6 +372,167 @@ static xbar_status solve_rows(xbar_s* h, int B, const double* dV, double* dI, do
     XB_CUDA(launch_orient_blvolt(m2, w2, dV, M, B, Bpad, rhs, st));
     if (dvWL) XB_CUDA(launch_orient_to_user(rhs, dvWL, M, N, Mp2, B, Bpad, st));  // original WL = mirror BL
     if (dvBL) XB_CUDA(launch_orient_to_user(w2, dvBL, M, N, Mp2, B, Bpad, st));   // original BL = mirror WL
+  }
+  return XBAR_OK;
+}
+
+// XBAR_FP32_IR solve of a row-blocked factorization: the refinement of xbar_solve run on the
+// mirror, with its sources on the bit-line chains (the residual's Vbl term) and the currents read
+// from its first block: after the initial solve and every update from the float-pair state, after
+// every correction from the correction itself (which also gives the stopping rule's |dI| / |I|).
+struct RowsIr {
+  int iters = 0;
+  double last = 0.0, prev = 0.0, rinf = 0.0;
+  bool converged = false;
+};
+static xbar_status solve_rows_mixed(xbar_s* h, int B, const double* dV, double* dI, double* dvWL, double* dvBL,
+                                    double tol, int max_iter, RowsIr* out) {
+  xbar_s* g = h->mirror;
+  const MapDev& m2 = g->m;
+  const int N = h->m.N, M2 = m2.M, Mp2 = m2.Mp, N2 = m2.N;
+  cudaStream_t st = h->st;
+  const bool cr = g->cr_active != 0;
+  const bool tc = g->tc_ready && !cr;
+  const int Bp = cr ? kCrPanel : tc ? kSweepTcPanel : sweep_panel_width<float>(Mp2, B, g->nsm);
+  const int Bpad = ((B + Bp - 1) / Bp) * Bp;
+  const size_t nst = (size_t)N2 * Mp2 * Bpad;
+  XB_CUDA(ensure(g->A, g->z, nst * 4));
+  XB_CUDA(ensure(g->A, g->dhat, nst * 4));
+  XB_CUDA(ensure(g->A, g->rhat, nst * 4));
+  XB_CUDA(ensure(g->A, g->w64, nst * 8));
+  XB_CUDA(ensure(g->A, g->phi, nst * 8));
+  XB_CUDA(ensure(g->A, g->maxrel, 16));
+  XB_CUDA(ensure(g->A, g->rmax, 16));
+  XB_CUDA(ensure(g->A, g->sI, (size_t)Bpad * N2 * 8));
+  ResidParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.M = M2;
+  rp.Mp = Mp2;
+  rp.N = N2;
+  rp.B = B;
+  rp.Bpad = Bpad;
+  rp.gs = m2.gs;
+  rp.gw = m2.gw;
+  rp.gb = m2.gb;
+  rp.go = m2.go;
+  rp.Gc = m2.Gc;
+  rp.dW = m2.dW;
+  rp.h = m2.h;
+  rp.tha = m2.tha;
+  rp.thc = m2.thc;
+  rp.s32 = m2.s32;
+  rp.V = nullptr;
+  rp.Vbl = dV;
+  rp.I = (double*)g->sI.p;  // the mirror's own current functional: scratch
+  rp.status = g->status;
+  rp.w = (double*)g->w64.p;
+  rp.w2 = (float2*)g->w64.p;
+  rp.dhat = (const float*)g->dhat.p;
+  rp.phi = (double*)g->phi.p;
+  rp.phi2 = (float2*)g->phi.p;
+  rp.Gc2 = m2.Gc2;
+  rp.h2 = m2.h2;
+  rp.tha2 = m2.tha2;
+  rp.thc2 = m2.thc2;
+  rp.rhat = (float*)g->rhat.p;
+  rp.rmax = (unsigned long long*)g->rmax.p;
+  SweepParams<float> sp;
+  sp.M = M2;
+  sp.Mp = Mp2;
+  sp.N = N2;
+  sp.B = B;
+  sp.Bp = Bp;
+  sp.Bpad = Bpad;
+  sp.X = (const float*)g->X.p;
+  sp.e = m2.e32;
+  sp.hs = m2.hs32;
+  sp.src = m2.src32;
+  sp.V = nullptr;
+  sp.rhs = (const float*)g->rhat.p;
+  sp.z = (float*)g->z.p;
+  sp.w = (float*)g->dhat.p;
+  sp.I = (double*)g->sI.p;
+  sp.accumulate = 0;
+  sp.max_rel = nullptr;
+  sp.status = g->status;
+  auto sweep32 = [&](int terms) -> cudaError_t {  // dhat = solve32(rhat) (rhat is overwritten by cyclic reduction)
+    if (tc) return launch_sweep_tc(sp, g->Xt.p, terms, st);
+    if (!cr) return launch_sweep<float>(sp, st);
+    CrSweepArgs<float> ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.B = B;
+    ca.Bpad = Bpad;
+    ca.V = nullptr;
+    ca.src = m2.src32;
+    ca.r = (float*)g->rhat.p;
+    ca.x = (float*)g->dhat.p;
+    ca.e = m2.e32;
+    ca.hs = m2.hs32;
+    ca.I = (double*)g->sI.p;
+    ca.tensor = use_cr_tensor(g) && Bpad >= 128;
+    return cr_sweep<float>(g, g->cr32, ca);
+  };
+  const int nsw = cr ? cr_sweep_launches(g, B, false) : 1;
+  {  // x0 = solve32(s o (V h')), the state w = s o x0, I from the state
+    PhaseScope ps(h, XBAR_PHASE_SWEEP, 1 + nsw + 1 + (tc ? 0 : 1));
+    XB_CUDA(launch_orient_rhs32(dV, m2.h, m2.s32, h->m.M, M2, Mp2, B, Bpad, (float*)g->rhat.p, st));
+    if (tc) {
+      sp.w = nullptr;
+      sp.w2out = rp.w2;
+      sp.s32 = m2.s32;
+      XB_CUDA(sweep32(kInitialTerms));
+      sp.w = (float*)g->dhat.p;
+      sp.w2out = nullptr;
+    } else {
+      XB_CUDA(sweep32(kInitialTerms));
+      XB_CUDA(launch_update(rp, 1, st));
+    }
+    XB_CUDA(launch_orient_state_currents(rp.w2, N, Bpad, B, m2.gs, dI, st));
+  }
+  bool w_current = true;
+  float mr = 0.0f;
+  for (int it = 0; it < max_iter; ++it) {
+    XB_CUDA(cudaMemsetAsync(g->rmax.p, 0, 8, st));
+    {
+      PhaseScope ps(h, XBAR_PHASE_RESID);
+      XB_CUDA(launch_resid(rp, st));  // rhat = s o (b - A w), sources on the bit-line chains
+    }
+    XB_CUDA(cudaMemsetAsync(g->maxrel.p, 0, 4, st));
+    {
+      PhaseScope ps(h, XBAR_PHASE_SWEEP, nsw + 1);
+      XB_CUDA(sweep32(correction_terms(it)));
+      XB_CUDA(launch_orient_correction_currents((const float*)g->dhat.p, m2.s32, N, Bpad, B, m2.gs, dI,
+                                                (float*)g->maxrel.p, g->status, st));
+    }
+    w_current = false;
+    ++out->iters;
+    unsigned long long rbits = 0;
+    XB_CUDA(cudaMemcpyAsync(&mr, g->maxrel.p, 4, cudaMemcpyDeviceToHost, st));
+    XB_CUDA(cudaMemcpyAsync(&rbits, g->rmax.p, 8, cudaMemcpyDeviceToHost, st));
+    XB_CUDA(cudaStreamSynchronize(st));
+    memcpy(&out->rinf, &rbits, 8);
+    out->prev = out->last;
+    out->last = mr;
+    if (!(mr == mr)) break;
+    const double rho = (it >= 1 && out->prev > 0.0) ? (double)mr / out->prev : 1.0;
+    if (mr <= tol || (rho <= 0.5 && (double)mr * rho / (1.0 - rho) <= tol)) {
+      out->converged = true;
+      break;
+    }
+    {
+      PhaseScope ps(h, XBAR_PHASE_UPDATE, 2);
+      XB_CUDA(launch_update(rp, 0, st));  // w += s o dhat
+      XB_CUDA(launch_orient_state_currents(rp.w2, N, Bpad, B, m2.gs, dI, st));
+    }
+    w_current = true;
+  }
+  if (dvWL || dvBL) {
+    PhaseScope ps(h, XBAR_PHASE_OUTPUT, 2 + (w_current ? 0 : 1) + (dvWL ? 1 : 0) + (dvBL ? 1 : 0));
+    if (!w_current) XB_CUDA(launch_update(rp, 0, st));
+    XB_CUDA(launch_pair_to_double(rp, st));  // the state as doubles, in place
+    XB_CUDA(launch_orient_blvolt(m2, rp.w, dV, h->m.M, B, Bpad, rp.phi, st));
+    if (dvWL) XB_CUDA(launch_orient_to_user(rp.phi, dvWL, h->m.M, N, Mp2, B, Bpad, st));
+    if (dvBL) XB_CUDA(launch_orient_to_user(rp.w, dvBL, h->m.M, N, Mp2, B, Bpad, st));
   }
   return XBAR_OK;
 }
@@ -455,10 +616,12 @@ xbar_status xbar::factor_handle(xbar_s* h, xbar_precision p, bool upload_params)
   h->orient_active = 0;
   if (use_rows(h, p)) {  // the mirrored crossbar (blocks over rows), factored in this handle's place
     PhaseScope ps(h, XBAR_PHASE_FACTOR, 1);
-    xbar_status s = factor_mirror(h);
+    xbar_status s = factor_mirror(h, p);
     if (s != XBAR_OK) return s;
     // map remap + assembly (3) + the factor (one launch, or the cyclic reduction's operations)
-    ps.nlaunch = 4 + (h->mirror->cr_active ? (int)h->mirror->cr64.ops.size() : 1);
+    const xbar_s* g = h->mirror;
+    ps.nlaunch = 4 + (g->cr_active ? (int)(p == XBAR_FP64 ? g->cr64.ops.size() : g->cr32.ops.size())
+                                   : 1 + g->tc_ready);
     h->orient_active = 1;
     h->cr_active = 0;
     h->tc_ready = 0;
@@ -564,17 +727,33 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
     dvBL = (double*)h->svBL.p;
   }
 
-  if (h->orient_active) {  // FP64, blocked over rows: the mirrored crossbar's solve
-    xbar_status s = solve_rows(h, B, dV, dI, dvWL, dvBL, true);
+  if (h->orient_active) {  // blocked over rows: the mirrored crossbar's solve
+    RowsIr ir;
+    xbar_status s = mixed ? solve_rows_mixed(h, B, dV, dI, dvWL, dvBL, tol, max_iter, &ir)
+                          : solve_rows(h, B, dV, dI, dvWL, dvBL, true);
     if (s != XBAR_OK) return s;
     if (!idev) XB_CUDA(cudaMemcpyAsync(I, dI, nIB * 8, cudaMemcpyDeviceToHost, st));
     if (vWL && !wdev) XB_CUDA(cudaMemcpyAsync(vWL, dvWL, nvolt * 8, cudaMemcpyDeviceToHost, st));
     if (vBL && !bdev) XB_CUDA(cudaMemcpyAsync(vBL, dvBL, nvolt * 8, cudaMemcpyDeviceToHost, st));
-    if (!idev || (vWL && !wdev) || (vBL && !bdev) || !vdev) {
+    if (mixed || !idev || (vWL && !wdev) || (vBL && !bdev) || !vdev) {
       xbar_status cs = check_status(h);
       if (cs != XBAR_OK) return cs;
     }
-    return XBAR_OK;  // info: zeros (no refinement)
+    if (info && mixed) {
+      info->iters = ir.iters;
+      info->max_rel_dI = ir.last;
+      info->resid_inf = ir.rinf;
+      double est = ir.last;
+      if (ir.iters >= 2 && ir.prev > 0.0) {
+        const double rate = ir.last / ir.prev;
+        if (rate < 1.0) est = ir.last * rate / (1.0 - rate);
+      }
+      info->err_est = est;
+    }
+    if (mixed && !ir.converged)
+      return fail(XBAR_ENOTCONV, "refinement stopped after %d corrections with max |dI|/|I| = %g > tol = %g",
+                  ir.iters, ir.last, tol);
+    return XBAR_OK;
   }
 
   const bool cr = h->cr_active != 0;
@@ -814,6 +993,8 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   MapDev& m = h->m;
   const int M = m.M, Mp = m.Mp, N = m.N;
   cudaStream_t st = h->st;
+  if (h->orient_active && h->prec != XBAR_FP64)
+    return fail(XBAR_ESTATE, "device-driven solves (tile batches) block over rows in XBAR_FP64 only");
   if (h->orient_active) {  // FP64, blocked over rows (stream-ordered launches only)
     if (!(h->irstate.p && h->irstate.bytes >= sizeof(IrState)) &&
         !(allow_alloc && ensure(h->A, h->irstate, sizeof(IrState)) == cudaSuccess))

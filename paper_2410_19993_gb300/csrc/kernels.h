@@ -129,6 +129,15 @@ cudaError_t launch_orient_currents(const double* w2, int N, int Bpad, int B, dou
 // the mirror's bit-line voltages u ([M][Mp2][Bpad]) from its word-line voltages w2 and the sources
 cudaError_t launch_orient_blvolt(const MapDev& m2, const double* w2, const double* V, int M, int B, int Bpad,
                                  double* u, cudaStream_t st);
+// mixed precision: equilibrated FP32 right-hand side s o (V h'), currents from the float-pair
+// state, and the correction's current change (I += dI, max |dI| / |I| into max_rel)
+cudaError_t launch_orient_rhs32(const double* V, const double* h2, const float* s32, int M, int M2, int Mp2, int B,
+                                int Bpad, float* rhs, cudaStream_t st);
+cudaError_t launch_orient_state_currents(const float2* w2, int N, int Bpad, int B, double gs2, double* I,
+                                         cudaStream_t st);
+cudaError_t launch_orient_correction_currents(const float* dhat, const float* s32, int N, int Bpad, int B,
+                                              double gs2, double* I, float* max_rel, unsigned* status,
+                                              cudaStream_t st);
 // out[b][i][j] = src2[M-1-i][N-1-j][b]
 cudaError_t launch_orient_to_user(const double* src2, double* out, int M, int N, int Mp2, int B, int Bpad,
                                   cudaStream_t st);
@@ -225,6 +234,7 @@ bool cr_supported(int Mp, int N);
 struct ResidParams {
   int M, Mp, N, B, Bpad;
   double gs, gw;
+  double gb, go;        // bit-line segment and sense conductances (bit-line sources only)
   const double* Gc;
   const double* dW;
   const double* h;
@@ -247,6 +257,10 @@ struct ResidParams {
   const float2* h2;
   const float2* tha2;
   const float2* thc2;
+  // sources on the bit-line chains instead (the mirrored crossbar of orient.cu): the word-line
+  // source potential is 0 (V unused) and the bottom node of bit line j is driven through g_o by
+  // Vbl[b][N-1-j] ([B][N]); nullptr: the usual sources V on the word lines
+  const double* Vbl;
 };
 // w = (first ? 0 : w) + s * dhat ; I = h . w    (float-pair state w2)
 cudaError_t launch_update(const ResidParams& p, int first, cudaStream_t st);

@@ -105,6 +105,76 @@ __global__ void orient_to_user_kernel(const double* __restrict__ src2, double* _
   }
 }
 
+// ---- the mirror in mixed precision (FP32 factor, float-pair refinement state) ---------------------
+// equilibrated right-hand side of the FP32 substitution: rhs[j'][i'][b] = s[j'][i'] V[b][M-1-j'] h'[j'][i']
+__global__ void orient_rhs32_kernel(const double* __restrict__ V, const double* __restrict__ h2,
+                                    const float* __restrict__ s32, int M, int M2, int Mp2, int B, int Bpad,
+                                    float* __restrict__ rhs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i2 = blockIdx.y, j2 = blockIdx.z;
+  if (b >= Bpad) return;
+  float v = 0.0f;
+  if (b < B && i2 < M2) {
+    const size_t c = (size_t)j2 * Mp2 + i2;
+    v = s32[c] * (float)(V[(size_t)b * M + (M - 1 - j2)] * h2[c]);
+  }
+  rhs[((size_t)j2 * Mp2 + i2) * Bpad + b] = v;
+}
+
+// I[b][j] = g_s' w'[0][N-1-j][b] from the float-pair state (hi + lo)
+__global__ void orient_state_currents_kernel(const float2* __restrict__ w2, int N, int Bpad, int B, double gs2,
+                                             double* __restrict__ I) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (b >= B) return;
+  const float2 w = w2[(size_t)(N - 1 - j) * Bpad + b];
+  I[(size_t)b * N + j] = gs2 * ((double)w.x + (double)w.y);
+}
+
+// the correction's current change dI = g_s' s[0][N-1-j] dhat[0][N-1-j][b]: I += dI and the maximum of
+// |dI| / |I| (atomic, non-negative floats) for the stopping rule
+__global__ void orient_correction_currents_kernel(const float* __restrict__ dhat, const float* __restrict__ s32,
+                                                  int N, int Bpad, int B, double gs2, double* __restrict__ I,
+                                                  float* __restrict__ max_rel, unsigned* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  float rel = 0.0f;
+  if (b < B) {
+    const int i2 = N - 1 - j;
+    const double d = gs2 * (double)s32[i2] * (double)dhat[(size_t)i2 * Bpad + b];
+    if (!isfinite(d)) set_status(status, XBAR_DEV_NONFINITE);
+    double* Ip = I + (size_t)b * N + j;
+    const double In = *Ip + d;
+    *Ip = In;
+    rel = (float)(fabs(d) / fmax(fabs(In), 1e-300));
+  }
+  const unsigned live = __activemask();
+  rel = __uint_as_float(__reduce_max_sync(live, __float_as_uint(rel)));
+  if ((threadIdx.x & 31) == __ffs(live) - 1 && max_rel && rel > 0.0f) atomic_max_nonneg(max_rel, rel);
+}
+
+cudaError_t launch_orient_rhs32(const double* V, const double* h2, const float* s32, int M, int M2, int Mp2, int B,
+                                int Bpad, float* rhs, cudaStream_t st) {
+  orient_rhs32_kernel<<<dim3((Bpad + 127) / 128, Mp2, M), 128, 0, st>>>(V, h2, s32, M, M2, Mp2, B, Bpad, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orient_state_currents(const float2* w2, int N, int Bpad, int B, double gs2, double* I,
+                                         cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  orient_state_currents_kernel<<<dim3((B + 127) / 128, N), 128, 0, st>>>(w2, N, Bpad, B, gs2, I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orient_correction_currents(const float* dhat, const float* s32, int N, int Bpad, int B,
+                                              double gs2, double* I, float* max_rel, unsigned* status,
+                                              cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  orient_correction_currents_kernel<<<dim3((B + 127) / 128, N), 128, 0, st>>>(dhat, s32, N, Bpad, B, gs2, I,
+                                                                               max_rel, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mirror_gc(const double* Gc, int M, int Mp, int N, double* Gc2, int Mp2, cudaStream_t st) {
   mirror_gc_kernel<<<dim3((Mp2 + 127) / 128, M), 128, 0, st>>>(Gc, M, Mp, N, Gc2, Mp2);
   return cudaGetLastError();

@@ -100,6 +100,8 @@ __global__ void resid_kernel(ResidParams p) {
     for (int i = 0; i < p.M; ++i) {
       const size_t o = (base + i) * p.Bpad + b;
       phi = padd(pmul(ld2(p.thc2, base + i), phi), pmul(ld2(p.tha2, base + i), ld2(p.w2, o)));
+      if (p.Vbl && i == p.M - 1 && b < p.B)  // g_o V / d_last, 1/d_last = thc_last / g_b
+        phi = padd(phi, pmul(split(p.go * p.thc[base + i] / p.gb), split(p.Vbl[(size_t)b * p.N + (p.N - 1 - j)])));
       st2(p.phi2, o, phi);
     }
   }
@@ -116,7 +118,7 @@ __global__ void resid_kernel(ResidParams p) {
     fp2 r = pmul(ld2(p.Gc2, base + i), psub(u, wi));
     if (has_l) r = padd(r, pmul(gw, psub(ld2(p.w2, o - col), wi)));
     if (has_r) r = padd(r, pmul(gw, psub(ld2(p.w2, o + col), wi)));
-    if (src) r = padd(r, pmul(gs, psub(split(p.V[(size_t)b * p.M + i]), wi)));
+    if (src) r = padd(r, pmul(gs, psub(p.Vbl ? fp2{0.0f, 0.0f} : split(p.V[(size_t)b * p.M + i]), wi)));
     const float rf = r.hi + r.lo;
     rmax = fmaxf(rmax, fabsf(rf));
     p.rhat[o] = rf * p.s32[base + i];

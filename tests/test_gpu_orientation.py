@@ -111,16 +111,38 @@ def test_rows_transfer_matrix():
     xb.destroy()
 
 
-def test_mixed_precision_keeps_columns_and_noalloc_refuses_rows():
-    """XBAR_FP32_IR factors block over columns whatever the option; the no-allocation entry point
-    needs a column-blocked FP64 factorization."""
+MIXED_SHAPES = [(128, 20, 300), (40, 3, 1000), (33, 17, 200), (200, 5, 40), (16, 128, 64), (1, 1, 1), (7, 1, 2),
+                (256, 32, 100)]
+
+
+@pytest.mark.parametrize("algorithm", ["thomas", "cr"])
+@pytest.mark.parametrize("M,N,B", MIXED_SHAPES)
+def test_rows_mixed_against_oracle(M, N, B, algorithm):
+    """XBAR_FP32_IR blocked over rows: FP32 factor of the mirror, float-pair refinement with the
+    sources on its bit-line chains, currents from its first block."""
+    G, V = case(M, N, B, None, seed=200 * M + N)
+    ref = oracle.solve(M, N, G, *R, V, voltages=True)
+    out = _solve(G, V, "rows", algorithm, precision="fp32_ir")
+    assert rel_err(out["I"], ref["I"]) <= MIXED_BAR
+    assert np.max(np.abs(out["vWL"] - ref["vWL"])) <= MIXED_BAR
+    assert np.max(np.abs(out["vBL"] - ref["vBL"])) <= MIXED_BAR
+    assert 1 <= out["info"]["iters"] <= 4
+    out["xb"].destroy()
+
+
+def test_mixed_auto_keeps_columns_and_noalloc_refuses_rows():
+    """Automatic orientation keeps mixed-precision factors on columns (bit for bit the column
+    result); the no-allocation entry point needs a column-blocked FP64 factorization."""
     M, N, B = 128, 20, 64
     G, V = case(M, N, B, None, seed=9)
     ref = oracle.solve(M, N, G, *R, V)
-    out = _solve(G, V, "rows", precision="fp32_ir", voltages=False)
-    assert rel_err(out["I"], ref["I"]) <= MIXED_BAR
-    xb = out["xb"]
-    xb.factor("fp64")  # rows
+    auto = _solve(G, V, "auto", precision="fp32_ir", voltages=False)
+    cols = _solve(G, V, "columns", precision="fp32_ir", voltages=False)
+    np.testing.assert_array_equal(auto["I"], cols["I"])
+    assert rel_err(auto["I"], ref["I"]) <= MIXED_BAR
+    cols["xb"].destroy()
+    xb = auto["xb"]
+    xb.factor("fp64")  # automatic: rows for FP64 (2N <= M)
     Vt = torch.from_numpy(np.ascontiguousarray(V)).cuda()
     I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
     with pytest.raises(xbar.XbarError) as e:
