@@ -55,6 +55,21 @@ __device__ __forceinline__ fp2 pmul(fp2 x, fp2 y) {
   e = fmaf(x.lo, y.hi, e);
   return quick_two_sum(p, e);
 }
+// The same transformations without the final renormalisation, for sums and products of terms of
+// one sign (no cancellation): hi + lo keeps the accuracy of the pair arithmetic above, while |lo|
+// may grow to a few ulp(hi).  Three FP32 operations fewer each; the residual is bound by issue
+// slots.  Differences that cancel (neighbouring node voltages) keep the normalised forms.
+__device__ __forceinline__ fp2 padd_u(fp2 x, fp2 y) {
+  const float s = x.hi + y.hi, v = s - x.hi;
+  return {s, ((x.hi - (s - v)) + (y.hi - v)) + (x.lo + y.lo)};
+}
+__device__ __forceinline__ fp2 pmul_u(fp2 x, fp2 y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return {p, e};
+}
 __device__ __forceinline__ fp2 ld2(const float2* a, size_t o) {
   const float2 v = a[o];
   return {v.x, v.y};
@@ -86,10 +101,10 @@ __global__ void update_kernel(ResidParams p, int first) {
 // Residual of the word-line rows (Eqs. 1, 2, 5, 6) as the sum of the branch currents into node
 // (i, j), each formed from a voltage difference (neighbouring voltages differ by millivolts, so
 // the differences keep full relative accuracy in pairs):
-//   r = [j > 0] g_w (w_{j-1} - w) + [j < N-1] g_w (w_{j+1} - w) + [j = 0] g_s (V_i - w) + G (u - w),
+//   r = g_w ([j > 0] (w_{j-1} - w) + [j < N-1] (w_{j+1} - w)) + [j = 0] g_s (V_i - w) + G (u - w),
 // identical to b + g_w (w_{j-1} + w_{j+1}) + G u - dW w.  u = T^-1 (G o w) by the bit-line chain
 // (forward phi_i = tha_i w_i + thc_i phi_{i-1}, back u_i = phi_i + thc_i u_{i+1}; all terms >= 0).
-__global__ void resid_kernel(ResidParams p) {
+__global__ void __launch_bounds__(128, 16) resid_kernel(ResidParams p) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
@@ -99,7 +114,8 @@ __global__ void resid_kernel(ResidParams p) {
     fp2 phi{0.0f, 0.0f};
     for (int i = 0; i < p.M; ++i) {
       const size_t o = (base + i) * p.Bpad + b;
-      phi = padd(pmul(ld2(p.thc2, base + i), phi), pmul(ld2(p.tha2, base + i), ld2(p.w2, o)));
+      // all terms >= 0 along the chain: unnormalised pairs
+      phi = padd_u(pmul_u(ld2(p.thc2, base + i), phi), pmul_u(ld2(p.tha2, base + i), ld2(p.w2, o)));
       if (p.Vbl && i == p.M - 1 && b < p.B)  // g_o V / d_last, 1/d_last = thc_last / g_b
         phi = padd(phi, pmul(split(p.go * p.thc[base + i] / p.gb), split(p.Vbl[(size_t)b * p.N + (p.N - 1 - j)])));
       st2(p.phi2, o, phi);
@@ -113,11 +129,16 @@ __global__ void resid_kernel(ResidParams p) {
   const size_t col = (size_t)p.Mp * p.Bpad;
   for (int i = p.M - 1; i >= 0; --i) {
     const size_t o = (base + i) * p.Bpad + b;
-    u = padd(ld2(p.phi2, o), pmul(ld2(p.thc2, base + i), u));
+    u = padd_u(ld2(p.phi2, o), pmul_u(ld2(p.thc2, base + i), u));
     const fp2 wi = ld2(p.w2, o);
-    fp2 r = pmul(ld2(p.Gc2, base + i), psub(u, wi));
-    if (has_l) r = padd(r, pmul(gw, psub(ld2(p.w2, o - col), wi)));
-    if (has_r) r = padd(r, pmul(gw, psub(ld2(p.w2, o + col), wi)));
+    fp2 r = pmul_u(ld2(p.Gc2, base + i), psub(u, wi));
+    // the two word-line branches as one product, g_w ((w_l - w) + (w_r - w)); the differences
+    // cancel, so they and the sums of r stay normalised
+    if (has_l || has_r) {
+      fp2 nb = has_l ? psub(ld2(p.w2, o - col), wi) : fp2{0.0f, 0.0f};
+      if (has_r) nb = has_l ? padd(nb, psub(ld2(p.w2, o + col), wi)) : psub(ld2(p.w2, o + col), wi);
+      r = padd(r, pmul_u(gw, nb));
+    }
     if (src) r = padd(r, pmul(gs, psub(p.Vbl ? fp2{0.0f, 0.0f} : split(p.V[(size_t)b * p.M + i]), wi)));
     const float rf = r.hi + r.lo;
     rmax = fmaxf(rmax, fabsf(rf));
