@@ -375,10 +375,10 @@ def run_xbar(args):
     traffic, traffic_note = None, None
     if dom == "sweep" and (M, N) == (256, 256) and bound == "tensor":
         # ncu DRAM read + write per sweep_tc_kernel launch at B = 2048 (the capture fits the size
-        # rule; the full batch does not), averaged over the solve's launches (2.192 GB initial,
-        # 2.206 GB for each correction), scaled by B / 2048: the kernel's streams are per vector,
-        # the factor blocks it re-reads come from L2
-        traffic = 2.201e9 * B / 2048
+        # rule; the full batch does not), averaged over the solve's launches (2.196 GB initial,
+        # 2.206 and 2.208 GB for the corrections), scaled by B / 2048: the kernel's streams are per
+        # vector, the factor blocks it re-reads come from L2
+        traffic = 2.203e9 * B / 2048
         traffic_note = (f"ncu dram__bytes_read+write at B=2048 (mean of the solve's three sweep launches) "
                         f"x B/2048 = {B / 2048:g}")
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
