@@ -157,7 +157,10 @@ __device__ __forceinline__ bool epi_sync_or(bool v) {
   return r != 0;
 }
 
-__host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 8 : 5; }
+// operand stages of kSub consecutive 16-wide K chunks each: one full/empty hand-off (wait, fence,
+// commit) per kSub chunks; the ring holds 96 KB (4 stages of 24 KB for 128 rows, 2 of 48 KB for 256)
+constexpr int kSub = 2;
+__host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 4 : 2; }
 
 // NH = number of 128-row halves of X_j (Mt = 128 NH); KP = number of BF16 terms of the split used
 // (1..3; the tiles always hold three, a sweep with fewer copies and multiplies only the leading
@@ -188,7 +191,9 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
   constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 2;  // one BF16 part of a chunk
   constexpr uint32_t chunk_bytes = kParts * part_bytes;
-  unsigned char* vb = xs + (size_t)NS * chunk_bytes;   // 24 column groups of lbo_b(Mt) bytes: [v0 | v1 | v2]
+  constexpr uint32_t stage_bytes = kSub * chunk_bytes;
+  static_assert((Mt / KC) % kSub == 0, "a stage must not span two column steps");
+  unsigned char* vb = xs + (size_t)NS * stage_bytes;   // 24 column groups of lbo_b(Mt) bytes: [v0 | v1 | v2]
   constexpr uint32_t LBO_B = lbo_b(Mt);
 
   constexpr int cps = Mt / KC;  // chunks per step
@@ -232,15 +237,19 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
     if (lane == 0) {
       long long issued = 0;
       int st = 0, use = 0, s = 0, kc = 0;  // stage, uses of this stage so far, step, chunk in step
-      for (long long c = 0; c < nchunks; ++c) {
+      const long long nstg = nchunks / kSub;  // cps is a multiple of kSub: a stage never spans two steps
+      for (long long c = 0; c < nstg; ++c) {
         if (c >= NS && !mbar_spin_bounded(&empty[st], (unsigned)((use - 1) & 1), p.status, wlim, 0))
           break;
         issued = c + 1;
         const int j = s < N ? s : 2 * N - 2 - s;
-        mbar_arrive_expect_tx(&full[st], copy_bytes);
-        bulk_g2s(xs + (size_t)st * chunk_bytes, Xt + ((size_t)j * cps + kc) * (chunk_bytes / 2), copy_bytes,
-                 &full[st]);
-        if (++kc == cps) { kc = 0; ++s; }
+        mbar_arrive_expect_tx(&full[st], kSub * copy_bytes);
+#pragma unroll
+        for (int sub = 0; sub < kSub; ++sub)
+          bulk_g2s(xs + (size_t)st * stage_bytes + sub * chunk_bytes,
+                   Xt + ((size_t)j * cps + kc + sub) * (chunk_bytes / 2), copy_bytes, &full[st]);
+        kc += kSub;
+        if (kc == cps) { kc = 0; ++s; }
         if (++st == NS) { st = 0; ++use; }
       }
       // before the block may exit: the last copy into each stage has landed (bounded wait)
@@ -258,29 +267,35 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       // MN-major, no swizzle: the descriptor's leading byte offset is the stride between groups of
       // 8 nodes (K), the stride byte offset the stride between groups of 8 columns (N)
       const uint64_t bdesc0 = umma::sdesc(smem_addr(vb), 128, LBO_B);
-      constexpr uint64_t a_stage = chunk_bytes >> 4, a_half = (16 * 128) >> 4, a_part = part_bytes >> 4;
+      constexpr uint64_t a_stage = stage_bytes >> 4, a_chunk = chunk_bytes >> 4, a_half = (16 * 128) >> 4,
+                         a_part = part_bytes >> 4;
       constexpr uint64_t b_term = ((uint64_t)(kBP / 8) * LBO_B) >> 4;  // v_q: 8 column groups per term
       uint64_t ast = adesc0;  // descriptor of stage mst
       for (int s = 0; s < nsteps; ++s) {
         bool ok = mbar_spin_bounded(vfull, (unsigned)(s & 1), p.status, wlim, 0);
         fence_after();
         uint64_t bdesc = bdesc0;  // advances by one K-step (2 node groups of 128 bytes) per chunk
-        for (int kc = 0; kc < cps && ok; ++kc) {
+        for (int kc0 = 0; kc0 < cps && ok; kc0 += kSub) {
           if (!mbar_spin_bounded(&full[mst], (unsigned)(muse & 1), p.status, wlim, 0)) {
             ok = false;
             break;
           }
           fence_after();
 #pragma unroll
-          for (int pt = 0; pt < KP; ++pt)  // A_pt v_q for pt + q < KP, all into the one accumulator
+          for (int sub = 0; sub < kSub; ++sub) {
+            const uint64_t ac = ast + sub * a_chunk;
 #pragma unroll
-            for (int qv = 0; qv + pt < KP; ++qv)
+            for (int pt = 0; pt < KP; ++pt)  // A_pt v_q for pt + q < KP, all into the one accumulator
 #pragma unroll
-              for (int hh = 0; hh < NH; ++hh)
-                umma::mma_bf16(tbase + (s & 1) * dset + hh * dcols, ast + pt * a_part + hh * a_half, bdesc + qv * b_term,
-                               umma::idesc_bf16(128, BP) | kBMajorMN, (kc > 0 || pt > 0 || qv > 0) ? 1u : 0u);
+              for (int qv = 0; qv + pt < KP; ++qv)
+#pragma unroll
+                for (int hh = 0; hh < NH; ++hh)
+                  umma::mma_bf16(tbase + (s & 1) * dset + hh * dcols, ac + pt * a_part + hh * a_half,
+                                 bdesc + qv * b_term, umma::idesc_bf16(128, BP) | kBMajorMN,
+                                 (kc0 + sub > 0 || pt > 0 || qv > 0) ? 1u : 0u);
+            bdesc += (uint64_t)((2 * 128) >> 4);
+          }
           mma_commit(&empty[mst]);
-          bdesc += (uint64_t)((2 * 128) >> 4);
           ast += a_stage;
           if (++mst == NS) { mst = 0; ++muse; ast = adesc0; }
         }
@@ -510,7 +525,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 
 size_t sweep_tc_smem_bytes(int Mt) {
   const int NS = tc_stages(Mt);
-  return 256 + 8 * 64 * 4 + (size_t)NS * (tc::kParts * tc::kKC * Mt * 2) + (size_t)tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt);
+  return 256 + 8 * 64 * 4 + (size_t)NS * kSub * (tc::kParts * tc::kKC * Mt * 2) +
+         (size_t)tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt);
 }
 
 bool sweep_tc_supported(int Mp) { return Mp <= 256; }
