@@ -157,10 +157,18 @@ __device__ __forceinline__ bool epi_sync_or(bool v) {
   return r != 0;
 }
 
-// operand stages of kSub consecutive 16-wide K chunks each: one full/empty hand-off (wait, fence,
-// commit) per kSub chunks; the ring holds 96 KB (4 stages of 24 KB for 128 rows, 2 of 48 KB for 256)
-constexpr int kSub = 2;
-__host__ __device__ constexpr int tc_stages(int Mt) { return Mt == 128 ? 4 : 2; }
+// Operand stages: each holds tc_sub consecutive 16-wide K chunks, a chunk slot only the KP terms a
+// sweep copies, so there is one full/empty hand-off (wait, fence, commit) per tc_sub chunks; as many
+// stages (2 to 8) as the shared memory beside the three-term vector operand holds.
+__host__ __device__ constexpr int tc_sub(int Mt, int KP) { return (Mt == 256 && KP == 3) ? 2 : 4; }
+__host__ __device__ constexpr uint32_t tc_slot(int Mt, int KP) { return (uint32_t)KP * tc::kKC * Mt * 2; }
+__host__ __device__ constexpr int tc_stages(int Mt, int KP) {
+  return (232448 - 2304 - (int)(tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt))) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP)) > 8
+             ? 8
+             : (232448 - 2304 - (int)(tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt))) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP));
+}
+static_assert(tc_stages(256, 2) == 2 && tc_stages(256, 3) == 2 && tc_stages(128, 2) == 5 && tc_stages(128, 3) == 3,
+              "stage rings");
 
 // NH = number of 128-row halves of X_j (Mt = 128 NH); KP = number of BF16 terms of the split used
 // (1..3; the tiles always hold three, a sweep with fewer copies and multiplies only the leading
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   using namespace tc;
   constexpr int BP = kBP, KC = kKC;
   constexpr int Mt = 128 * NH, nh = NH;
-  constexpr int NS = tc_stages(Mt);
+  constexpr int NS = tc_stages(Mt, KP), kSub = tc_sub(Mt, KP);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b0 = blockIdx.x * BP;
   const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
@@ -191,7 +199,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   unsigned char* xs = smem + 256 + 8 * 64 * 4;         // [NS stages][hi | lo]
   constexpr uint32_t part_bytes = (uint32_t)KC * Mt * 2;  // one BF16 part of a chunk
   constexpr uint32_t chunk_bytes = kParts * part_bytes;
-  constexpr uint32_t stage_bytes = kSub * chunk_bytes;
+  constexpr uint32_t slot_bytes = tc_slot(Mt, KP);  // one chunk's KP terms in shared memory
+  constexpr uint32_t stage_bytes = kSub * slot_bytes;
   static_assert((Mt / KC) % kSub == 0, "a stage must not span two column steps");
   unsigned char* vb = xs + (size_t)NS * stage_bytes;   // 24 column groups of lbo_b(Mt) bytes: [v0 | v1 | v2]
   constexpr uint32_t LBO_B = lbo_b(Mt);
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
         mbar_arrive_expect_tx(&full[st], kSub * copy_bytes);
 #pragma unroll
         for (int sub = 0; sub < kSub; ++sub)
-          bulk_g2s(xs + (size_t)st * stage_bytes + sub * chunk_bytes,
+          bulk_g2s(xs + (size_t)st * stage_bytes + sub * slot_bytes,
                    Xt + ((size_t)j * cps + kc + sub) * (chunk_bytes / 2), copy_bytes, &full[st]);
         kc += kSub;
         if (kc == cps) { kc = 0; ++s; }
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       // MN-major, no swizzle: the descriptor's leading byte offset is the stride between groups of
       // 8 nodes (K), the stride byte offset the stride between groups of 8 columns (N)
       const uint64_t bdesc0 = umma::sdesc(smem_addr(vb), 128, LBO_B);
-      constexpr uint64_t a_stage = stage_bytes >> 4, a_chunk = chunk_bytes >> 4, a_half = (16 * 128) >> 4,
+      constexpr uint64_t a_stage = stage_bytes >> 4, a_chunk = slot_bytes >> 4, a_half = (16 * 128) >> 4,
                          a_part = part_bytes >> 4;
       constexpr uint64_t b_term = ((uint64_t)(kBP / 8) * LBO_B) >> 4;  // v_q: 8 column groups per term
       uint64_t ast = adesc0;  // descriptor of stage mst
@@ -523,9 +532,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   if (warp == 1) tmem_dealloc(tbase, ncols);
 }
 
-size_t sweep_tc_smem_bytes(int Mt) {
-  const int NS = tc_stages(Mt);
-  return 256 + 8 * 64 * 4 + (size_t)NS * kSub * (tc::kParts * tc::kKC * Mt * 2) +
+size_t sweep_tc_smem_bytes(int Mt, int KP) {
+  return 256 + 8 * 64 * 4 + (size_t)tc_stages(Mt, KP) * tc_sub(Mt, KP) * tc_slot(Mt, KP) +
          (size_t)tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt);
 }
 
@@ -551,8 +559,8 @@ cudaError_t launch_sweep_tc(const SweepParams<float>& p, const void* Xt, int ter
   if (p.Bp != tc::kBP || p.Bpad % tc::kBP) return cudaErrorInvalidValue;
   const int blocks = (p.B + tc::kBP - 1) / tc::kBP;
   if (blocks == 0) return cudaSuccess;
-  const size_t smem = sweep_tc_smem_bytes(Mt);
   if (terms < 1 || terms > tc::kParts) return cudaErrorInvalidValue;
+  const size_t smem = sweep_tc_smem_bytes(Mt, terms);
   using Kern = void (*)(SweepParams<float>, const __nv_bfloat16*);
   const Kern kerns[2][3] = {{sweep_tc_kernel<1, 1>, sweep_tc_kernel<1, 2>, sweep_tc_kernel<1, 3>},
                             {sweep_tc_kernel<2, 1>, sweep_tc_kernel<2, 2>, sweep_tc_kernel<2, 3>}};
