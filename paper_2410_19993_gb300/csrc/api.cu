@@ -404,6 +404,7 @@ static xbar_status solve_rows_mixed(xbar_s* h, int B, const double* dV, double* 
   XB_CUDA(ensure(g->A, g->maxrel, 16));
   XB_CUDA(ensure(g->A, g->rmax, 16));
   XB_CUDA(ensure(g->A, g->sI, (size_t)Bpad * N2 * 8));
+  if (tc) XB_CUDA(ensure(g->A, g->w1, nst * 4));
   ResidParams rp;
   memset(&rp, 0, sizeof(rp));
   rp.M = M2;
@@ -476,18 +477,19 @@ static xbar_status solve_rows_mixed(xbar_s* h, int B, const double* dV, double* 
   {  // x0 = solve32(s o (V h')), the state w = s o x0, I from the state
     PhaseScope ps(h, XBAR_PHASE_SWEEP, 1 + nsw + 1 + (tc ? 0 : 1));
     XB_CUDA(launch_orient_rhs32(dV, m2.h, m2.s32, h->m.M, M2, Mp2, B, Bpad, (float*)g->rhat.p, st));
-    if (tc) {
+    if (tc) {  // the sweep writes the state (FP32) itself; the first update turns it into pairs
       sp.w = nullptr;
-      sp.w2out = rp.w2;
+      sp.w1out = (float*)g->w1.p;
       sp.s32 = m2.s32;
       XB_CUDA(sweep32(kInitialTerms));
       sp.w = (float*)g->dhat.p;
-      sp.w2out = nullptr;
+      sp.w1out = nullptr;
+      rp.w1 = (const float*)g->w1.p;
     } else {
       XB_CUDA(sweep32(kInitialTerms));
       XB_CUDA(launch_update(rp, 1, st));
     }
-    XB_CUDA(launch_orient_state_currents(rp.w2, N, Bpad, B, m2.gs, dI, st));
+    XB_CUDA(launch_orient_state_currents(rp.w2, rp.w1, N, Bpad, B, m2.gs, dI, st));
   }
   bool w_current = true;
   float mr = 0.0f;
@@ -521,8 +523,9 @@ static xbar_status solve_rows_mixed(xbar_s* h, int B, const double* dV, double* 
     }
     {
       PhaseScope ps(h, XBAR_PHASE_UPDATE, 2);
-      XB_CUDA(launch_update(rp, 0, st));  // w += s o dhat
-      XB_CUDA(launch_orient_state_currents(rp.w2, N, Bpad, B, m2.gs, dI, st));
+      XB_CUDA(launch_update(rp, 0, st));  // w += s o dhat (into the pairs)
+      rp.w1 = nullptr;
+      XB_CUDA(launch_orient_state_currents(rp.w2, nullptr, N, Bpad, B, m2.gs, dI, st));
     }
     w_current = true;
   }
@@ -888,14 +891,16 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       ca.tensor = use_cr_tensor(h) && Bpad >= 128;  // wide batches: products on the tensor cores
       return cr_sweep<float>(h, h->cr32, ca);
     };
-    if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 as float pairs itself
+    if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 (FP32) itself
       PhaseScope ps(h, XBAR_PHASE_SWEEP);
+      XB_CUDA(ensure(h->A, h->w1, nst * 4));
       sp.w = nullptr;
-      sp.w2out = rp.w2;
+      sp.w1out = (float*)h->w1.p;
       sp.s32 = m.s32;
       XB_CUDA(launch_sweep_tc(sp, h->Xt.p, kInitialTerms, st));
       sp.w = (float*)h->dhat.p;
-      sp.w2out = nullptr;
+      sp.w1out = nullptr;
+      rp.w1 = (const float*)h->w1.p;  // read as (w, 0) until the first update writes the pairs
     } else {
       {
         PhaseScope ps(h, XBAR_PHASE_SWEEP, cr ? cr_sweep_launches(h, B, true) : 1);
@@ -911,7 +916,7 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       XB_CUDA(cudaMemsetAsync(h->rmax.p, 0, 8, st));
       {
         PhaseScope ps(h, XBAR_PHASE_RESID);
-        XB_CUDA(launch_resid(rp, st));          // rhat = s o (b - A w)   [FP64]
+        XB_CUDA(launch_resid(rp, st));          // rhat = s o (b - A w)   [float pairs]
       }
       XB_CUDA(cudaMemsetAsync(h->maxrel.p, 0, 4, st));
       sp.V = nullptr;
@@ -943,8 +948,9 @@ extern "C" xbar_status xbar_solve(xbar_t h, int B, const double* V, double* I, d
       }
       {
         PhaseScope ps(h, XBAR_PHASE_UPDATE);
-        XB_CUDA(launch_update(rp, 0, st));      // w += s o dhat, I = h . w   [FP64]
+        XB_CUDA(launch_update(rp, 0, st));      // w += s o dhat, I = h . w   [float pairs]
       }
+      rp.w1 = nullptr;
       w_current = true;
     }
     if (want_v && !w_current) {
@@ -1048,13 +1054,15 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
     return tc ? launch_sweep_tc(sp, h->Xt.p, terms, st) : launch_sweep<float>(sp, st);
   };
   XB_CUDA(launch_ir_init(state, st));
-  if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 as float pairs itself
+  if (tc) {  // x0 = solve32(b); the sweep writes the state w = s o x0 (FP32) itself
+    if (!need(h->w1, nst * 4)) return fail(XBAR_ENOMEM, "workspace not prepared for this batch size");
     sp.w = nullptr;
-    sp.w2out = rp.w2;
+    sp.w1out = (float*)h->w1.p;
     sp.s32 = m.s32;
     XB_CUDA(sweep(kInitialTerms));
     sp.w = (float*)h->dhat.p;
-    sp.w2out = nullptr;
+    sp.w1out = nullptr;
+    rp.w1 = (const float*)h->w1.p;  // read as (w, 0) until the first update writes the pairs
   } else {
     XB_CUDA(sweep(kInitialTerms));       // x0 = solve32(b)
     XB_CUDA(launch_update(rp, 1, st));   // w = s o dhat, I = h . w
@@ -1066,10 +1074,11 @@ xbar_status xbar::solve_device_driven(xbar_s* h, int B, const double* dV, double
   sp.skip = &state->done;
   rp.skip = &state->done;
   for (int it = 0; it < max_iter; ++it) {
-    XB_CUDA(launch_resid(rp, st));       // rhat = s o (b - A w)   [FP64]  (skipped once converged)
+    XB_CUDA(launch_resid(rp, st));       // rhat = s o (b - A w)   [float pairs]  (skipped once converged)
     XB_CUDA(sweep(correction_terms(it)));  // dhat = solve32(rhat), I += dI
     XB_CUDA(launch_ir_check(state, tol, st));
     XB_CUDA(launch_update(rp, 0, st));   // w += s o dhat, I = h . w   (skipped once converged)
+    rp.w1 = nullptr;                     // later passes read the pairs the update wrote
   }
   return XBAR_OK;
 }

@@ -121,6 +121,7 @@ struct xbar_s {
   int tc_ready = 0;
   // solve workspace
   xbar::Buf z, dhat, rhat, w64, phi, maxrel, rmax, irstate;
+  xbar::Buf w1;  // FP32 refinement state written by the initial tensor-core sweep
   // staging for host pointers
   xbar::Buf sV, sI, svWL, svBL;
   // block cyclic reduction (cr.cu): plans of both precisions; cr_active = factored by it

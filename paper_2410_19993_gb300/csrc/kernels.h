@@ -96,9 +96,9 @@ struct SweepParams {
   float* max_rel;      // atomic max of |dI| / |I| (accumulate mode), or nullptr
   unsigned* status;
   const int* skip = nullptr;  // if set and nonzero at launch, the kernel does nothing
-  // tensor-core sweep only: write the refinement state w2 = (s32 o w, 0) as float pairs
-  // ([N][Mp][Bpad]) instead of w, so that the first update pass is not needed
-  float2* w2out = nullptr;
+  // tensor-core sweep only: write the refinement state s32 o w as FP32 ([N][Mp][Bpad]; its
+  // float-pair low part is 0) instead of w, so that the first update pass is not needed
+  float* w1out = nullptr;
   const float* s32 = nullptr;  // [N][Mp]
 };
 
@@ -133,8 +133,8 @@ cudaError_t launch_orient_blvolt(const MapDev& m2, const double* w2, const doubl
 // state, and the correction's current change (I += dI, max |dI| / |I| into max_rel)
 cudaError_t launch_orient_rhs32(const double* V, const double* h2, const float* s32, int M, int M2, int Mp2, int B,
                                 int Bpad, float* rhs, cudaStream_t st);
-cudaError_t launch_orient_state_currents(const float2* w2, int N, int Bpad, int B, double gs2, double* I,
-                                         cudaStream_t st);
+cudaError_t launch_orient_state_currents(const float2* w2, const float* w1, int N, int Bpad, int B, double gs2,
+                                         double* I, cudaStream_t st);
 cudaError_t launch_orient_correction_currents(const float* dhat, const float* s32, int N, int Bpad, int B,
                                               double gs2, double* I, float* max_rel, unsigned* status,
                                               cudaStream_t st);
@@ -257,6 +257,9 @@ struct ResidParams {
   const float2* h2;
   const float2* tha2;
   const float2* thc2;
+  // the refinement state as FP32 (low part 0, as the initial tensor-core sweep writes it) instead
+  // of w2, for the first residual and the first update (which writes w2); nullptr: w2
+  const float* w1;
   // sources on the bit-line chains instead (the mirrored crossbar of orient.cu): the word-line
   // source potential is 0 (V unused) and the bottom node of bit line j is driven through g_o by
   // Vbl[b][N-1-j] ([B][N]); nullptr: the usual sources V on the word lines

@@ -121,14 +121,15 @@ __global__ void orient_rhs32_kernel(const double* __restrict__ V, const double* 
   rhs[((size_t)j2 * Mp2 + i2) * Bpad + b] = v;
 }
 
-// I[b][j] = g_s' w'[0][N-1-j][b] from the float-pair state (hi + lo)
-__global__ void orient_state_currents_kernel(const float2* __restrict__ w2, int N, int Bpad, int B, double gs2,
-                                             double* __restrict__ I) {
+// I[b][j] = g_s' w'[0][N-1-j][b] from the float-pair state (hi + lo), or from its FP32 form w1
+__global__ void orient_state_currents_kernel(const float2* __restrict__ w2, const float* __restrict__ w1, int N,
+                                             int Bpad, int B, double gs2, double* __restrict__ I) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (b >= B) return;
-  const float2 w = w2[(size_t)(N - 1 - j) * Bpad + b];
-  I[(size_t)b * N + j] = gs2 * ((double)w.x + (double)w.y);
+  const size_t o = (size_t)(N - 1 - j) * Bpad + b;
+  const double w = w1 ? (double)w1[o] : (double)w2[o].x + (double)w2[o].y;
+  I[(size_t)b * N + j] = gs2 * w;
 }
 
 // the correction's current change dI = g_s' s[0][N-1-j] dhat[0][N-1-j][b]: I += dI and the maximum of
@@ -159,10 +160,10 @@ cudaError_t launch_orient_rhs32(const double* V, const double* h2, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_orient_state_currents(const float2* w2, int N, int Bpad, int B, double gs2, double* I,
-                                         cudaStream_t st) {
+cudaError_t launch_orient_state_currents(const float2* w2, const float* w1, int N, int Bpad, int B, double gs2,
+                                         double* I, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  orient_state_currents_kernel<<<dim3((B + 127) / 128, N), 128, 0, st>>>(w2, N, Bpad, B, gs2, I);
+  orient_state_currents_kernel<<<dim3((B + 127) / 128, N), 128, 0, st>>>(w2, w1, N, Bpad, B, gs2, I);
   return cudaGetLastError();
 }
 

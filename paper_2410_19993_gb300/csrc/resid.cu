@@ -75,6 +75,16 @@ __device__ __forceinline__ fp2 ld2(const float2* a, size_t o) {
   return {v.x, v.y};
 }
 __device__ __forceinline__ void st2(float2* a, size_t o, fp2 v) { a[o] = make_float2(v.hi, v.lo); }
+// the refinement state at o: float pairs, or (kW1) the FP32 state the initial tensor-core sweep
+// writes; for the update, whichever the parameters hold
+template <bool kW1>
+__device__ __forceinline__ fp2 ldw(const ResidParams& p, size_t o) {
+  if constexpr (kW1) return fp2{p.w1[o], 0.0f};
+  else return ld2(p.w2, o);
+}
+__device__ __forceinline__ fp2 ldw_any(const ResidParams& p, size_t o) {
+  return p.w1 ? ldw<true>(p, o) : ldw<false>(p, o);
+}
 __device__ __forceinline__ fp2 split(double x) {
   const float hi = (float)x;
   return {hi, (float)(x - (double)hi)};
@@ -91,7 +101,7 @@ __global__ void update_kernel(ResidParams p, int first) {
   for (int i = 0; i < p.M; ++i) {
     const size_t o = (base + i) * p.Bpad + b;
     const float d = p.s32[base + i] * p.dhat[o];
-    const fp2 wn = first ? fp2{d, 0.0f} : padd(ld2(p.w2, o), fp2{d, 0.0f});
+    const fp2 wn = first ? fp2{d, 0.0f} : padd(ldw_any(p, o), fp2{d, 0.0f});
     st2(p.w2, o, wn);
     Iacc = padd(Iacc, pmul(ld2(p.h2, base + i), wn));
   }
@@ -104,6 +114,7 @@ __global__ void update_kernel(ResidParams p, int first) {
 //   r = g_w ([j > 0] (w_{j-1} - w) + [j < N-1] (w_{j+1} - w)) + [j = 0] g_s (V_i - w) + G (u - w),
 // identical to b + g_w (w_{j-1} + w_{j+1}) + G u - dW w.  u = T^-1 (G o w) by the bit-line chain
 // (forward phi_i = tha_i w_i + thc_i phi_{i-1}, back u_i = phi_i + thc_i u_{i+1}; all terms >= 0).
+template <bool kW1>
 __global__ void __launch_bounds__(128, 16) resid_kernel(ResidParams p) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(128, 16) resid_kernel(ResidParams p) {
     for (int i = 0; i < p.M; ++i) {
       const size_t o = (base + i) * p.Bpad + b;
       // all terms >= 0 along the chain: unnormalised pairs
-      phi = padd_u(pmul_u(ld2(p.thc2, base + i), phi), pmul_u(ld2(p.tha2, base + i), ld2(p.w2, o)));
+      phi = padd_u(pmul_u(ld2(p.thc2, base + i), phi), pmul_u(ld2(p.tha2, base + i), ldw<kW1>(p, o)));
       if (p.Vbl && i == p.M - 1 && b < p.B)  // g_o V / d_last, 1/d_last = thc_last / g_b
         phi = padd(phi, pmul(split(p.go * p.thc[base + i] / p.gb), split(p.Vbl[(size_t)b * p.N + (p.N - 1 - j)])));
       st2(p.phi2, o, phi);
@@ -130,13 +141,13 @@ __global__ void __launch_bounds__(128, 16) resid_kernel(ResidParams p) {
   for (int i = p.M - 1; i >= 0; --i) {
     const size_t o = (base + i) * p.Bpad + b;
     u = padd_u(ld2(p.phi2, o), pmul_u(ld2(p.thc2, base + i), u));
-    const fp2 wi = ld2(p.w2, o);
+    const fp2 wi = ldw<kW1>(p, o);
     fp2 r = pmul_u(ld2(p.Gc2, base + i), psub(u, wi));
     // the two word-line branches as one product, g_w ((w_l - w) + (w_r - w)); the differences
     // cancel, so they and the sums of r stay normalised
     if (has_l || has_r) {
-      fp2 nb = has_l ? psub(ld2(p.w2, o - col), wi) : fp2{0.0f, 0.0f};
-      if (has_r) nb = has_l ? padd(nb, psub(ld2(p.w2, o + col), wi)) : psub(ld2(p.w2, o + col), wi);
+      fp2 nb = has_l ? psub(ldw<kW1>(p, o - col), wi) : fp2{0.0f, 0.0f};
+      if (has_r) nb = has_l ? padd(nb, psub(ldw<kW1>(p, o + col), wi)) : psub(ldw<kW1>(p, o + col), wi);
       r = padd(r, pmul_u(gw, nb));
     }
     if (src) r = padd(r, pmul(gs, psub(p.Vbl ? fp2{0.0f, 0.0f} : split(p.V[(size_t)b * p.M + i]), wi)));
@@ -204,7 +215,8 @@ cudaError_t launch_pair_to_double(const ResidParams& p, cudaStream_t st) {
 
 cudaError_t launch_resid(const ResidParams& p, cudaStream_t st) {
   dim3 grid((p.Bpad + 127) / 128, p.N);
-  resid_kernel<<<grid, 128, 0, st>>>(p);
+  if (p.w1) resid_kernel<true><<<grid, 128, 0, st>>>(p);
+  else resid_kernel<false><<<grid, 128, 0, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
                             : 0.0f;
       const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
-      const float sj = (real && p.w2out) ? p.s32[(size_t)j * Mp + i] : 0.0f;
+      const float sj = (real && p.w1out) ? p.s32[(size_t)j * Mp + i] : 0.0f;
       const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
       const bool have_w = !fwd || s == N - 1;
       const bool more = s + 1 < nsteps;
@@ -484,10 +484,11 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
             for (int n = 0; n < 32; n += 4)
               *reinterpret_cast<float4*>(p.w + o + n) =
                   make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
-          if (p.w2out && real)  // refinement state (s o w, 0) as float pairs
+          if (p.w1out && real)  // refinement state s o w (FP32; the float pairs' low part is 0)
 #pragma unroll
-            for (int n = 0; n < 32; n += 2)
-              *reinterpret_cast<float4*>(p.w2out + o + n) = make_float4(sj * a[n], 0.0f, sj * a[n + 1], 0.0f);
+            for (int n = 0; n < 32; n += 4)
+              *reinterpret_cast<float4*>(p.w1out + o + n) =
+                  make_float4(sj * a[n], sj * a[n + 1], sj * a[n + 2], sj * a[n + 3]);
 #pragma unroll
           for (int n = 0; n < 32; ++n) a[n] *= hj;
           dots[blk] = transpose_sum32(a, lane);
