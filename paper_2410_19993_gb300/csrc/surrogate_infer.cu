@@ -8,13 +8,15 @@
 // c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when an estimate of vector b is above the bound.
 //
 // Persistent blocks (one per SM, 128 threads): W2 (256 x 256 BF16, 128 KB) is staged once into
-// shared memory as the B operand; each 128-row tile's operand h1 (64 KB) is generated from P, Q
-// and b1 by the threads (thread = row, so a warp's 16-byte stores cover 32 consecutive rows and
-// are bank-conflict free); one thread issues 16 MMAs (M = 128, N = 256, K = 16) into one of two
-// 256-column tensor-memory accumulators; while the tensor core works on tile t, the threads
-// drain tile t-1's accumulator (tcgen05.ld), apply b2, ReLU and the BF16 rounding of h2, reduce
-// against W3 and write the prediction.  Every wait is bounded; on expiry the block records
-// XBAR_DEV_TIMEOUT, waits (bounded) for its own MMAs and frees its tensor memory.
+// shared memory as the B operand.  A tile is 128 rows = 8 vectors x 16 bit lines, so its operand
+// h1 needs only 16 rows of P and 8 rows of Q (24 KB): they are copied into shared memory with
+// cp.async while the previous tile's epilogue runs, and the threads build h1 (64 KB) from them
+// (thread = row, a warp's 16-byte stores cover 32 consecutive rows: bank-conflict free).  One
+// thread issues 16 MMAs (M = 128, N = 256, K = 16) into one of two 256-column tensor-memory
+// accumulators; while the tensor core works on tile t, the threads drain tile t-1's accumulator
+// (tcgen05.ld), apply b2, ReLU and the BF16 rounding of h2, reduce against W3 and write the
+// prediction.  Every wait is bounded; on expiry the block records XBAR_DEV_TIMEOUT, waits
+// (bounded) for its own MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -35,7 +37,18 @@ constexpr uint32_t kLA = (kRows / 8) * 128;  // A: K-direction stride between co
 constexpr uint32_t kLB = (kH / 8) * 128;     // B: same for 256 rows (4 KB)
 constexpr uint32_t kBBytes = (kH / 8) * kLB;    // 128 KB
 constexpr uint32_t kABytes = (kH / 8) * kLA;    // 64 KB
-constexpr size_t kSmem = 1024 + kBBytes + kABytes + (size_t)(2 * kH + 2 * kH) * 4;
+constexpr int kTJ = 16, kTB = kRows / kTJ;      // a tile: kTB vectors x kTJ bit lines
+constexpr int kPPitch = kH + 4;                 // P rows in shared memory (bank offset 4 per row)
+constexpr size_t kPBytes = (size_t)kTJ * kPPitch * 4, kQBytes = (size_t)kTB * kH * 4;
+constexpr size_t kSmem = 1024 + kBBytes + kABytes + (size_t)(2 * kH + 2 * kH) * 4 + kPBytes + kQBytes;
+static_assert(kSmem <= 232448, "shared memory");
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t a_off(int m, int g) { return (uint32_t)g * kLA + (uint32_t)(m >> 3) * 128 + (uint32_t)(m & 7) * 16; }
 __device__ __forceinline__ uint32_t b_off(int n, int g) { return (uint32_t)g * kLB + (uint32_t)(n >> 3) * 128 + (uint32_t)(n & 7) * 16; }
@@ -46,7 +59,8 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   using namespace si;
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
-  const long ntiles = (p.rows + kRows - 1) / kRows;
+  const long Bv = p.rows / p.N;  // input vectors
+  const long njt = (p.N + kTJ - 1) / kTJ, ntiles = ((Bv + kTB - 1) / kTB) * njt;
 
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm);  // [2]: MMA of the tile in accumulator 0 / 1
@@ -56,6 +70,25 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   float* b1s = reinterpret_cast<float*>(As + kABytes);
   float* b2s = b1s + kH;
   float* w3s = b2s + kH;  // [2][kH]
+  float* Ps = w3s + 2 * kH;          // [kTJ][kPPitch] rows of P of the tile's bit lines
+  float* Qs = Ps + kTJ * kPPitch;    // [kTB][kH] rows of Q of the tile's vectors
+  // rows of P and Q of tile t into Ps, Qs (16-byte cp.async, zero fill past N or B)
+  auto stage_rows = [&](long t) {
+    const long b0 = (t / njt) * kTB, j0 = (t % njt) * kTJ;
+#pragma unroll
+    for (int u = 0; u < kTJ * (kH / 4) / kThreads; ++u) {
+      const int id = tid + kThreads * u, rr = id / (kH / 4), c = id % (kH / 4);
+      const long j = j0 + rr;
+      cp_async16(Ps + rr * kPPitch + 4 * c, p.P + (j < p.N ? j : 0) * kH + 4 * c, j < p.N ? 16u : 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kTB * (kH / 4) / kThreads; ++u) {
+      const int id = tid + kThreads * u, qq = id / (kH / 4), c = id % (kH / 4);
+      const long b = b0 + qq;
+      cp_async16(Qs + qq * kH + 4 * c, p.Q + (b < Bv ? b : 0) * kH + 4 * c, b < Bv ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -94,7 +127,9 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   long prev = -1;
   // drain accumulator `buf` (tile t): b2, ReLU, BF16 rounding, W3, prediction
   auto epilogue = [&](long t, int buf) {
-    const long r = t * kRows + tid;
+    const long b = (t / njt) * kTB + (tid >> 4), j = (t % njt) * kTJ + (tid & 15);
+    const bool real = b < Bv && j < p.N;
+    const long r = b * p.N + j;
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll 1
     for (int cb = 0; cb < kH; cb += 32) {
@@ -107,31 +142,32 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
         s1 = fmaf(w3s[kH + cb + q], h, s1);
       }
     }
-    if (r < p.rows) {
+    if (real) {
       const double ii = p.Iid[r];
       const float n0 = s0 + p.b3[0], n1 = s1 + p.b3[1];
       const double Ir = p.Iln[r] + ii * (p.mu + p.sigma * (double)n0);
       const double e = p.cal * p.sigma * (double)expf(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
       p.I[r] = Ir;
       if (p.est) p.est[r] = e;
-      if (p.flag && !(e <= p.bound)) p.flag[r / p.N] = 1;
+      if (p.flag && !(e <= p.bound)) p.flag[b] = 1;
     }
   };
 
+  if (blockIdx.x < ntiles) stage_rows(blockIdx.x);
   for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int buf = issued & 1;
     // the previous tile's MMAs read the operand buffer: wait for them before regenerating it
     if (issued >= 1)
       ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
                              wlim, 20);
+    cp_async_wait_all();  // this thread's copies of tile t's rows; the barrier shows everyone's
     if (__syncthreads_or(!ok)) break;
     umma::fence_after();
-    {  // operand of tile t: thread = row m
-      const long r = t * kRows + tid;
-      const bool real = r < p.rows;
-      const long b = real ? r / p.N : 0, j = real ? r - b * p.N : 0;
-      const float4* P4 = reinterpret_cast<const float4*>(p.P + j * kH);
-      const float4* Q4 = reinterpret_cast<const float4*>(p.Q + b * kH);
+    {  // operand of tile t: thread = row m = (vector qq, bit line rr), from the staged rows
+      const long b = (t / njt) * kTB + (tid >> 4), j = (t % njt) * kTJ + (tid & 15);
+      const bool real = b < Bv && j < p.N;
+      const float4* P4 = reinterpret_cast<const float4*>(Ps + (tid & 15) * kPPitch);
+      const float4* Q4 = reinterpret_cast<const float4*>(Qs + (tid >> 4) * kH);
       const float4* C4 = reinterpret_cast<const float4*>(b1s);
 #pragma unroll
       for (int g0 = 0; g0 < kH / 8; g0 += 4) {
@@ -167,6 +203,8 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
       umma::commit(&bar[buf]);
     }
     ++issued;
+    // the next tile's rows: Ps and Qs were last read before the barrier above
+    if (t + gridDim.x < ntiles) stage_rows(t + gridDim.x);
     if (prev >= 0) epilogue(prev, (issued - 2) & 1);  // overlaps the MMAs just issued
     umma::fence_before();
     prev = t;
@@ -178,6 +216,7 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
     umma::fence_after();
     if (ok) epilogue(prev, (issued - 1) & 1);
   }
+  cp_async_wait_all();  // no copy may still be in flight when the block exits
   if (!ok && issued >= 1)  // the last commit covers every MMA of this block: wait for it (bounded)
     mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status, wlim, 20);
   umma::fence_before();
@@ -188,7 +227,7 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
 cudaError_t launch_surrogate_infer(const SurInferParams& p, int nsm, cudaStream_t st) {
   if (p.rows <= 0) return cudaSuccess;
   if (p.N < 1 || !p.P || !p.Q || !p.W2 || !p.I) return cudaErrorInvalidValue;
-  const long ntiles = (p.rows + si::kRows - 1) / si::kRows;
+  const long ntiles = ((p.rows / p.N + si::kTB - 1) / si::kTB) * ((p.N + si::kTJ - 1) / si::kTJ);
   const int grid = (int)std::min<long>(ntiles, nsm > 0 ? nsm : 1);
   cudaError_t e = cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)si::kSmem);
