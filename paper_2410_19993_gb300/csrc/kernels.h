@@ -176,7 +176,8 @@ struct SurInferParams {
   const float* P;                   // [>= N][256]  per-column part of the first layer
   const float* Q;                   // [>= B][256]  per-vector part of the first layer
   const float* b1;                  // [256]
-  const struct __nv_bfloat16* W2;   // [256][256] (output unit, input unit)
+  const struct __nv_bfloat16* W2;   // [256][256] (output unit, input unit) in the kernel's B-operand
+                                    // layout (launch_surrogate_w2_tile)
   const float* b2;                  // [256]
   const float* W3;                  // [2][256]
   const float* b3;                  // [2]
@@ -189,6 +190,8 @@ struct SurInferParams {
   unsigned* status;
 };
 cudaError_t launch_surrogate_infer(const SurInferParams& p, int nsm, cudaStream_t st);
+// W2 (BF16 [256][256], row = output unit) -> W2t (128 KB) in the layout launch_surrogate_infer reads
+cudaError_t launch_surrogate_w2_tile(const struct __nv_bfloat16* W2, void* W2t, cudaStream_t st);
 
 // ---- batched GEMM job lists (gemm_jobs.cu, gemm_jobs_tc.cu) -----------------------------------
 // One job: C = Cin + alpha * sum_s op(A_s) op(B_s)   (Cin may be NULL: then C = alpha * sum; Cin

@@ -592,6 +592,7 @@ struct xbar_surrogate_s {
   long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, np = 0;
   float *P = nullptr, *Gr = nullptr, *Am = nullptr, *Av = nullptr;
   __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+  __nv_bfloat16* W2t = nullptr;  // W2b in the inference kernel's operand layout
   double* loss = nullptr;  // [2]
   double cal = 1.0;                 // error-estimate scale (calibration)
   double mu = 0.0, sigma = 1.0;     // target standardisation (set by the first training call)
@@ -631,6 +632,7 @@ static xbar_status refresh_bf16(xbar_surrogate_t s) {
   to_bf16_kernel<<<(n1 + 255) / 256, 256, 0, s->st>>>(s->P + s->oW1, s->W1b, n1);
   to_bf16_kernel<<<(n2 + 255) / 256, 256, 0, s->st>>>(s->P + s->oW2, s->W2b, n2);
   XB_CUDA(cudaGetLastError());
+  XB_CUDA(launch_surrogate_w2_tile(s->W2b, s->W2t, s->st));
   return XBAR_OK;
 }
 
@@ -681,6 +683,7 @@ extern "C" xbar_status xbar_surrogate_create(int M, int N, double R_s, double R_
   if (s->A.alloc((void**)&s->P, s->np * 4) || s->A.alloc((void**)&s->Gr, s->np * 4) ||
       s->A.alloc((void**)&s->Am, s->np * 4) || s->A.alloc((void**)&s->Av, s->np * 4) ||
       s->A.alloc((void**)&s->W1b, (size_t)kH * s->Fp * 2) || s->A.alloc((void**)&s->W2b, (size_t)kH * kH * 2) ||
+      s->A.alloc((void**)&s->W2t, (size_t)kH * kH * 2) ||
       s->A.alloc((void**)&s->loss, 16) || s->A.alloc((void**)&s->status, sizeof(DevStatus)))
     return bail(set_error(XBAR_ENOMEM, "surrogate parameters"));
   // He initialisation of the weights (padding columns of W1 stay zero), zero biases, small head
@@ -1063,7 +1066,7 @@ static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, lo
   q.P = (const float*)s->Pm.p;
   q.Q = (const float*)s->Qm.p;
   q.b1 = s->P + s->ob1;
-  q.W2 = s->W2b;
+  q.W2 = s->W2t;
   q.b2 = s->P + s->ob2;
   q.W3 = s->P + s->oW3;
   q.b3 = s->P + s->ob3;

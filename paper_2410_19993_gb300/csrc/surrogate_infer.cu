@@ -7,8 +7,8 @@
 // and the prediction I = I_line + I_ideal (mu + sigma n0) with the relative error estimate
 // c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when an estimate of vector b is above the bound.
 //
-// Persistent blocks (one per SM, 128 threads): W2 (256 x 256 BF16, 128 KB) is staged once into
-// shared memory as the B operand.  A tile is 128 rows = 8 vectors x 16 bit lines, so its operand
+// Persistent blocks (one per SM, 128 threads): W2 (256 x 256 BF16, 128 KB), pre-tiled in global
+// memory in the B operand's layout whenever the weights change, is copied once into shared memory.  A tile is 128 rows = 8 vectors x 16 bit lines, so its operand
 // h1 needs only 16 rows of P and 8 rows of Q (24 KB): they are copied into shared memory with
 // cp.async while the previous tile's epilogue runs, and the threads build h1 (64 KB) from them
 // (thread = row, a warp's 16-byte stores cover 32 consecutive rows: bank-conflict free).  One
@@ -96,24 +96,17 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
     fence_mbar_init();
   }
   if (warp == 0) umma::alloc(tslot, 2 * kH);
-  // W2 (row n = output unit, k = input unit) into the B layout; thread = row, two passes
-  for (int n = tid; n < kH; n += kThreads) {
-    const uint4* src = reinterpret_cast<const uint4*>(p.W2 + (size_t)n * kH);
-#pragma unroll
-    for (int g0 = 0; g0 < kH / 8; g0 += 8) {
-      uint4 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = src[g0 + u];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) *reinterpret_cast<uint4*>(Bs + b_off(n, g0 + u)) = v[u];
-    }
-  }
+  // W2, already in the B layout (launch_surrogate_w2_tile): 16-byte copies, all in flight at once
+  for (uint32_t x = tid; x < kBBytes / 16; x += kThreads)
+    cp_async16(Bs + 16 * x, reinterpret_cast<const unsigned char*>(p.W2) + 16 * x, 16u);
+  cp_async_commit();
   for (int k = tid; k < kH; k += kThreads) {
     b1s[k] = p.b1[k];
     b2s[k] = p.b2[k];
     w3s[k] = p.W3[k];
     w3s[kH + k] = p.W3[kH + k];
   }
+  cp_async_wait_all();
   fence_proxy_async_smem();
   umma::fence_before();
   __syncthreads();
@@ -222,6 +215,21 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   umma::fence_before();
   __syncthreads();
   if (warp == 0) umma::dealloc(tbase, 2 * kH);
+}
+
+// W2 (row n = output unit, column k = input unit, BF16 [256][256]) -> the kernel's B-operand layout
+// (core matrices of 8 rows x 16 bytes, K-direction stride kLB): 16 bytes per thread
+__global__ void surrogate_w2_tile_kernel(const __nv_bfloat16* __restrict__ W2, unsigned char* __restrict__ W2t) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;  // (n, g): 8 consecutive k of row n
+  if (x >= si::kH * (si::kH / 8)) return;
+  const int n = x / (si::kH / 8), g = x % (si::kH / 8);
+  *reinterpret_cast<uint4*>(W2t + si::b_off(n, g)) = reinterpret_cast<const uint4*>(W2 + (size_t)n * si::kH)[g];
+}
+
+cudaError_t launch_surrogate_w2_tile(const __nv_bfloat16* W2, void* W2t, cudaStream_t st) {
+  const int n = si::kH * (si::kH / 8);
+  surrogate_w2_tile_kernel<<<(n + 255) / 256, 256, 0, st>>>(W2, static_cast<unsigned char*>(W2t));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_surrogate_infer(const SurInferParams& p, int nsm, cudaStream_t st) {
