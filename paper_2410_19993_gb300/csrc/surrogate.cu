@@ -133,11 +133,15 @@ __global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sG
   const int i = i0 + r;
   const double* g = gsm + r * P;
   float* rd = rsm + r * P;
-  double acc = 0.0;
+  // The suffix sums S are a network feature (rounded to BF16 there): an FP32 sum of positive
+  // terms is ample, and it keeps the FP64 pipe (1/64 of FP32 here) off this sequential loop; each
+  // conductance is converted to FP32 once.
+  float acc = 0.0f;
+  const float sc = (float)s_scale;
   float a = 0.0f, b = 1.0f;  // delta = a / b
   for (int j0 = N - 1; j0 >= 0; j0 -= kU) {
     const int n = min(kU, j0 + 1);
-    float bj[kU], dj[kU];
+    float bj[kU], dj[kU], gf[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       if (u < n) {
@@ -145,6 +149,7 @@ __global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sG
         const float num = ((j0 - u) == 0 ? gs : gw) * b + gv * b + gw * a;  // D_j b_j
         bj[u] = b;
         dj[u] = num;
+        gf[u] = gv;
         a = gv * b + gw * a;
         b = num;
       }
@@ -154,12 +159,11 @@ __global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sG
       if (u < n) {
         const int j = j0 - u;
         const long o = (long)j * M + i;
-        const double gd = g[j];
         const float w = bj[u] / dj[u];
-        Gt[o] = gd;
-        Gf[o] = (float)gd;
-        acc += gd;
-        St[o] = (float)(acc * s_scale);
+        Gt[o] = g[j];
+        Gf[o] = gf[u];
+        acc += gf[u];
+        St[o] = acc * sc;
         wl[o] = w;
         rd[j] = w;
       }
