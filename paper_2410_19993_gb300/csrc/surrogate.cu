@@ -113,6 +113,34 @@ __device__ __forceinline__ void stage_block(T* dst, int n, S src, D di) {
   }
 }
 
+// dst[(t / M) P + t % M] = src[t] for t < M N, when M is a multiple of 4 and src 16-byte aligned:
+// float4 loads (kStage of them in flight per thread: four times the bytes of stage_block), scalar
+// stores into the odd-pitch rows
+__device__ __forceinline__ void stage_pitch4(float* dst, const float* src, int M, int N, int P) {
+  const int n4 = M * N / 4;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  for (int t0 = threadIdx.x; t0 < n4; t0 += kStage * blockDim.x) {
+    float4 v[kStage];
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < n4) v[u] = s4[t];
+    }
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < n4) {
+        const int e = 4 * t, r = e / M, c = e - r * M;
+        float* d = dst + r * P + c;
+        d[0] = v[u].x;
+        d[1] = v[u].y;
+        d[2] = v[u].z;
+        d[3] = v[u].w;
+      }
+    }
+  }
+}
+
 // One thread per word line, blockDim.x (<= 32) lines per block; their conductances and pivots in
 // shared memory (pitch N + 1).  Dynamic shared memory: blockDim.x (N + 1) (8 + 4) bytes.
 __global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sGj, int M, int N, float gs, float gw,
@@ -281,7 +309,10 @@ __global__ void line_smem_kernel(const float* __restrict__ Gf, const float* __re
   float* Gs = Fs + N * P;
   float* As = Gs + N * P;
   auto stage = [&](float* dst, const float* src) {
-    stage_block(dst, M * N, [&](int t) { return src[t]; }, [&](int t) { return (t / M) * P + t % M; });
+    if ((M & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0)
+      stage_pitch4(dst, src, M, N, P);
+    else
+      stage_block(dst, M * N, [&](int t) { return src[t]; }, [&](int t) { return (t / M) * P + t % M; });
   };
   stage(Gs, Gf);
   stage_block(Fs, M * N, [&](int t) { return t % M == k ? tau[t] : 0.0f; },
