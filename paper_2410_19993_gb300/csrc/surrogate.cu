@@ -141,6 +141,29 @@ __device__ __forceinline__ void stage_pitch4(float* dst, const float* src, int M
   }
 }
 
+// the same for doubles: dst[(t / N) P + t % N] = src[t], t < rows N, N even, src 16-byte aligned
+__device__ __forceinline__ void stage_pitch2d(double* dst, const double* src, int N, int rows, int P) {
+  const int n2 = rows * N / 2;
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+  for (int t0 = threadIdx.x; t0 < n2; t0 += kStage * blockDim.x) {
+    double2 v[kStage];
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < n2) v[u] = s2[t];
+    }
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < n2) {
+        const int e = 2 * t, r = e / N, c = e - r * N;
+        dst[r * P + c] = v[u].x;
+        dst[r * P + c + 1] = v[u].y;
+      }
+    }
+  }
+}
+
 // One thread per word line, blockDim.x (<= 32) lines per block; their conductances and pivots in
 // shared memory (pitch N + 1).  Dynamic shared memory: blockDim.x (N + 1) (8 + 4) bytes.
 __global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sGj, int M, int N, float gs, float gw,
@@ -149,7 +172,10 @@ __global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sG
   extern __shared__ double gsm[];
   const int i0 = blockIdx.x * blockDim.x, rows = min((int)blockDim.x, M - i0), P = N + 1;
   float* rsm = reinterpret_cast<float*>(gsm + blockDim.x * P);
-  if (sGj == 1)  // consecutive threads along a row
+  const double* g0 = G + (long)i0 * sGi;
+  if (sGj == 1 && sGi == N && (N & 1) == 0 && (reinterpret_cast<uintptr_t>(g0) & 15) == 0)
+    stage_pitch2d(gsm, g0, N, rows, P);  // contiguous rows: 16-byte loads
+  else if (sGj == 1)  // consecutive threads along a row
     stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t / N) * sGi + t % N]; },
                 [&](int t) { return (t / N) * P + t % N; });
   else           // consecutive threads down a column
@@ -214,8 +240,12 @@ __global__ void prep_cols_kernel(const float* __restrict__ Gf, int M, int N, flo
   const int j0 = blockIdx.x * blockDim.x, cols = min((int)blockDim.x, N - j0), P = M + 1;
   float* gsm = csm;                   // G, then g_o z G
   float* esm = csm + blockDim.x * P;  // 1/E
-  stage_block(gsm, cols * M, [&](int t) { return Gf[(long)j0 * M + t]; },
-              [&](int t) { return (t / M) * P + t % M; });
+  const float* gf0 = Gf + (long)j0 * M;
+  if ((M & 3) == 0 && (reinterpret_cast<uintptr_t>(gf0) & 15) == 0)
+    stage_pitch4(gsm, gf0, M, cols, P);
+  else
+    stage_block(gsm, cols * M, [&](int t) { return Gf[(long)j0 * M + t]; },
+                [&](int t) { return (t / M) * P + t % M; });
   __syncthreads();
   const int c = threadIdx.x;
   if (c < cols) {
