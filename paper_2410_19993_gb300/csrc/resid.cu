@@ -70,6 +70,23 @@ __device__ __forceinline__ fp2 pmul_u(fp2 x, fp2 y) {
   e = fmaf(x.lo, y.hi, e);
   return {p, e};
 }
+// x - y for a difference that goes into a product: the exact two-sum of the leading parts plus the
+// difference of the trailing ones, not renormalised (pmul_u accepts a trailing part of a few ulp)
+__device__ __forceinline__ fp2 psub_u(fp2 x, fp2 y) {
+  const fp2 t = two_sum(x.hi, -y.hi);
+  return {t.hi, t.lo + (x.lo - y.lo)};
+}
+// (l - w) + (r - w), not renormalised: three exact two-sums of the leading parts, the trailing
+// parts and the rounding errors summed once
+__device__ __forceinline__ fp2 pdiff2_u(fp2 l, fp2 r, fp2 w) {
+  const fp2 a = two_sum(l.hi, -w.hi), c = two_sum(r.hi, -w.hi), s = two_sum(a.hi, c.hi);
+  return {s.hi, s.lo + ((a.lo + c.lo) + fmaf(-2.0f, w.lo, l.lo + r.lo))};
+}
+// the FP32 rounding of x + y: the exact two-sum of the leading parts, then everything else
+__device__ __forceinline__ float psum_f(fp2 x, fp2 y) {
+  const fp2 t = two_sum(x.hi, y.hi);
+  return t.hi + (t.lo + (x.lo + y.lo));
+}
 __device__ __forceinline__ fp2 ld2(const float2* a, size_t o) {
   const float2 v = a[o];
   return {v.x, v.y};
@@ -114,47 +131,158 @@ __global__ void update_kernel(ResidParams p, int first) {
 //   r = g_w ([j > 0] (w_{j-1} - w) + [j < N-1] (w_{j+1} - w)) + [j = 0] g_s (V_i - w) + G (u - w),
 // identical to b + g_w (w_{j-1} + w_{j+1}) + G u - dW w.  u = T^-1 (G o w) by the bit-line chain
 // (forward phi_i = tha_i w_i + thc_i phi_{i-1}, back u_i = phi_i + thc_i u_{i+1}; all terms >= 0).
+//
+// The chain is walked in segments of kSeg rows so that phi never makes a round trip through
+// memory per node: a first forward walk keeps only the value entering each segment (one pair per
+// kSeg nodes, in the phi scratch), then the back walk takes the segments last to first.  For each
+// it loads the segment's state and its two neighbour columns at once (one memory latency per
+// segment, not per row), recomputes phi from the stored entry value (the same operations, so the
+// same bits), forms the word-line branch terms, and walks the segment backwards.  Per node and
+// vector the state is read twice and the residual written once (20 bytes, against 36 with phi
+// stored per node); the neighbour columns are read by the blocks of columns j +- 1 at about the
+// same time and come from L2.
+constexpr int kSeg = 4;  // rows per segment of the back walk
+constexpr int kFwd = 4;  // segments per batch of loads in the forward walk
+
+__device__ __forceinline__ fp2 phi_step(float2 thc, float2 tha, fp2 phi, fp2 w) {
+  // all terms >= 0 along the chain: unnormalised pairs
+  return padd_u(pmul_u(fp2{thc.x, thc.y}, phi), pmul_u(fp2{tha.x, tha.y}, w));
+}
+
+// one (column, vector) chain of the state: row i at w[i rs + d], d selecting a neighbour column
 template <bool kW1>
-__global__ void __launch_bounds__(128, 16) resid_kernel(ResidParams p) {
+struct StateCol {
+  const float* w1;
+  const float2* w2;
+  size_t rs;
+  __device__ __forceinline__ fp2 at(int i, long d = 0) const {
+    const long o = (long)i * (long)rs + d;
+    if constexpr (kW1) {
+      return fp2{w1[o], 0.0f};
+    } else {
+      const float2 v = w2[o];
+      return {v.x, v.y};
+    }
+  }
+};
+
+// the column's coefficients, staged in shared memory by each block
+struct ColCoef {
+  const float2 *thc, *tha, *Gc;
+  const float* s;
+};
+
+// Back walk of one segment (rows i0 .. i0+n-1, kTail: the last, possibly short one).  kNb: which
+// word-line neighbours exist (1 left, 2 right, 3 both).
+template <bool kW1, int kNb, bool kTail>
+__device__ __forceinline__ void back_segment(const ResidParams& p, const ColCoef& c, const StateCol<kW1>& W,
+                                             long col, float* rh, fp2 f, int i0, int n, int j, int b, bool src,
+                                             fp2 gw, fp2 gs, fp2& u, float& rmax) {
+  fp2 wv[kSeg], e[kSeg], ph[kSeg];
+  fp2 wl[kSeg], wr[kSeg];
+#pragma unroll
+  for (int q = 0; q < kSeg; ++q) {
+    if (!kTail || q < n) {
+      wv[q] = W.at(i0 + q);
+      if (kNb & 1) wl[q] = W.at(i0 + q, -col);
+      if (kNb & 2) wr[q] = W.at(i0 + q, col);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kSeg; ++q) {
+    if (!kTail || q < n) {
+      const int i = i0 + q;
+      f = phi_step(c.thc[i], c.tha[i], f, wv[q]);
+      if (kTail && p.Vbl && i == p.M - 1 && b < p.B)  // g_o V / d_last, 1/d_last = thc_last / g_b
+        f = padd(f, pmul(split(p.go * ((double)c.thc[i].x + (double)c.thc[i].y) / p.gb), split(p.Vbl[(size_t)b * p.N + (p.N - 1 - j)])));
+      ph[q] = f;
+      // the word-line branches g_w ((w_l - w) + (w_r - w)) and the source branch: terms whose
+      // differences cancel, summed in pairs
+      if constexpr (kNb == 3) e[q] = pmul_u(gw, pdiff2_u(wl[q], wr[q], wv[q]));
+      else if constexpr (kNb == 1) e[q] = pmul_u(gw, psub_u(wl[q], wv[q]));
+      else if constexpr (kNb == 2) e[q] = pmul_u(gw, psub_u(wr[q], wv[q]));
+      else e[q] = fp2{0.0f, 0.0f};
+      if (kNb != 1 && kNb != 3 && src)
+        e[q] = padd(e[q], pmul(gs, psub(p.Vbl ? fp2{0.0f, 0.0f} : split(p.V[(size_t)b * p.M + i]), wv[q])));
+    }
+  }
+#pragma unroll
+  for (int q = kSeg - 1; q >= 0; --q) {
+    if (!kTail || q < n) {
+      const int i = i0 + q;
+      const float2 t = c.thc[i], g = c.Gc[i];
+      u = padd_u(ph[q], pmul_u(fp2{t.x, t.y}, u));
+      const float rf = psum_f(pmul_u(fp2{g.x, g.y}, psub_u(u, wv[q])), e[q]);
+      rmax = fmaxf(rmax, fabsf(rf));
+      rh[(long)i * (long)W.rs] = rf * c.s[i];
+    }
+  }
+}
+
+template <bool kW1, int kNb>
+__device__ __forceinline__ void back_walk(const ResidParams& p, const ColCoef& c, const StateCol<kW1>& W, long col,
+                                          float* rh, const float2* ph2, int S, int j, int b, fp2& u, float& rmax) {
+  const bool src = (kNb == 0 || kNb == 2) && j == 0 && b < p.B;
+  const fp2 gw = split(p.gw), gs = split(p.gs);
+  const int last = (S - 1) * kSeg;
+  auto entry = [&](int s) {
+    if (s == 0) return fp2{0.0f, 0.0f};
+    const float2 v = ph2[(long)s * (long)W.rs];
+    return fp2{v.x, v.y};
+  };
+  back_segment<kW1, kNb, true>(p, c, W, col, rh, entry(S - 1), last, p.M - last, j, b, src, gw, gs, u, rmax);
+  for (int s = S - 2; s >= 0; --s)
+    back_segment<kW1, kNb, false>(p, c, W, col, rh, entry(s), s * kSeg, kSeg, j, b, src, gw, gs, u, rmax);
+}
+
+template <bool kW1>
+__global__ void __launch_bounds__(128, 7) resid_kernel(ResidParams p) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
-  if (b >= p.Bpad || j >= p.N) return;
   const size_t base = (size_t)j * p.Mp;
+  const int M = p.M, S = (M + kSeg - 1) / kSeg;  // segments; only the last may be short
+  // the column's coefficients: thc, tha, Gc pairs and s, 28 bytes per row
+  extern __shared__ float2 csm[];
+  const ColCoef c{csm, csm + M, csm + 2 * M, reinterpret_cast<const float*>(csm + 3 * M)};
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    csm[t] = p.thc2[base + t];
+    csm[M + t] = p.tha2[base + t];
+    csm[2 * M + t] = p.Gc2[base + t];
+    reinterpret_cast<float*>(csm + 3 * M)[t] = p.s32[base + t];
+  }
+  __syncthreads();
+  if (b >= p.Bpad) return;
+  const size_t rs = p.Bpad, o0 = base * rs + b;
+  const StateCol<kW1> W{kW1 ? p.w1 + o0 : nullptr, kW1 ? nullptr : p.w2 + o0, rs};
+  float2* ph2 = p.phi2 + o0;  // phi entering segment s (s >= 1) at ph2[s rs]
+  // forward walk: segments 0 .. S-2 are full; keep the value entering each segment
   {
     fp2 phi{0.0f, 0.0f};
-    for (int i = 0; i < p.M; ++i) {
-      const size_t o = (base + i) * p.Bpad + b;
-      // all terms >= 0 along the chain: unnormalised pairs
-      phi = padd_u(pmul_u(ld2(p.thc2, base + i), phi), pmul_u(ld2(p.tha2, base + i), ldw<kW1>(p, o)));
-      if (p.Vbl && i == p.M - 1 && b < p.B)  // g_o V / d_last, 1/d_last = thc_last / g_b
-        phi = padd(phi, pmul(split(p.go * p.thc[base + i] / p.gb), split(p.Vbl[(size_t)b * p.N + (p.N - 1 - j)])));
-      st2(p.phi2, o, phi);
+    for (int s = 0; s + 1 < S; s += kFwd) {
+      const int nr = min(kFwd, S - 1 - s) * kSeg, i0 = s * kSeg;
+      fp2 wv[kFwd * kSeg];
+#pragma unroll
+      for (int q = 0; q < kFwd * kSeg; ++q)
+        if (q < nr) wv[q] = W.at(i0 + q);
+#pragma unroll
+      for (int q = 0; q < kFwd * kSeg; ++q) {
+        if (q < nr) {
+          phi = phi_step(c.thc[i0 + q], c.tha[i0 + q], phi, wv[q]);
+          if (q % kSeg == kSeg - 1) ph2[(long)(s + q / kSeg + 1) * (long)rs] = make_float2(phi.hi, phi.lo);
+        }
+      }
     }
   }
   const bool has_l = j > 0, has_r = j + 1 < p.N;
-  const bool src = (j == 0) && (b < p.B);
-  const fp2 gw = split(p.gw), gs = split(p.gs);
+  const long col = (long)p.Mp * (long)rs;
+  float* rh = p.rhat + o0;
   fp2 u{0.0f, 0.0f};
   float rmax = 0.0f;  // |r| tracked in FP32: only its magnitude is reported
-  const size_t col = (size_t)p.Mp * p.Bpad;
-  for (int i = p.M - 1; i >= 0; --i) {
-    const size_t o = (base + i) * p.Bpad + b;
-    u = padd_u(ld2(p.phi2, o), pmul_u(ld2(p.thc2, base + i), u));
-    const fp2 wi = ldw<kW1>(p, o);
-    fp2 r = pmul_u(ld2(p.Gc2, base + i), psub(u, wi));
-    // the two word-line branches as one product, g_w ((w_l - w) + (w_r - w)); the differences
-    // cancel, so they and the sums of r stay normalised
-    if (has_l || has_r) {
-      fp2 nb = has_l ? psub(ldw<kW1>(p, o - col), wi) : fp2{0.0f, 0.0f};
-      if (has_r) nb = has_l ? padd(nb, psub(ldw<kW1>(p, o + col), wi)) : psub(ldw<kW1>(p, o + col), wi);
-      r = padd(r, pmul_u(gw, nb));
-    }
-    if (src) r = padd(r, pmul(gs, psub(p.Vbl ? fp2{0.0f, 0.0f} : split(p.V[(size_t)b * p.M + i]), wi)));
-    const float rf = r.hi + r.lo;
-    rmax = fmaxf(rmax, fabsf(rf));
-    p.rhat[o] = rf * p.s32[base + i];
-  }
+  if (has_l && has_r) back_walk<kW1, 3>(p, c, W, col, rh, ph2, S, j, b, u, rmax);
+  else if (has_l) back_walk<kW1, 1>(p, c, W, col, rh, ph2, S, j, b, u, rmax);
+  else if (has_r) back_walk<kW1, 2>(p, c, W, col, rh, ph2, S, j, b, u, rmax);
+  else back_walk<kW1, 0>(p, c, W, col, rh, ph2, S, j, b, u, rmax);
   if (!(rmax <= 3.0e38f)) set_status(p.status, XBAR_DEV_NONFINITE);
   // warp max of |r| over the lanes still running (those past Bpad have left), then one atomic per
   // warp: non-negative floats and doubles order like their bit patterns
@@ -215,8 +343,9 @@ cudaError_t launch_pair_to_double(const ResidParams& p, cudaStream_t st) {
 
 cudaError_t launch_resid(const ResidParams& p, cudaStream_t st) {
   dim3 grid((p.Bpad + 127) / 128, p.N);
-  if (p.w1) resid_kernel<true><<<grid, 128, 0, st>>>(p);
-  else resid_kernel<false><<<grid, 128, 0, st>>>(p);
+  const size_t smem = (size_t)p.M * 28;  // M <= 1024: within the default 48 KB
+  if (p.w1) resid_kernel<true><<<grid, 128, smem, st>>>(p);
+  else resid_kernel<false><<<grid, 128, smem, st>>>(p);
   return cudaGetLastError();
 }
 
