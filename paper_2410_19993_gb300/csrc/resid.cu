@@ -107,20 +107,49 @@ __device__ __forceinline__ fp2 split(double x) {
   return {hi, (float)(x - (double)hi)};
 }
 
-// w = (first ? 0 : w) + s * dhat,  I[b][j] = h_j . w_j   (float pairs; I written as a double)
-__global__ void update_kernel(ResidParams p, int first) {
+// w = (first ? 0 : w) + s * dhat,  I[b][j] = h_j . w_j   (float pairs; I written as a double).
+// Rows are taken kUpd at a time with all their loads issued before the first store, so a thread
+// waits for memory once per batch rather than once per row.
+constexpr int kUpd = 8;
+__global__ void __launch_bounds__(128, 8) update_kernel(ResidParams p, int first) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (b >= p.Bpad || j >= p.N) return;
-  const size_t base = (size_t)j * p.Mp;
+  const size_t base = (size_t)j * p.Mp, rs = p.Bpad, o0 = base * rs + b;
+  const float* dh = p.dhat + o0;
+  float2* w2 = p.w2 + o0;
+  const float* w1 = p.w1 ? p.w1 + o0 : nullptr;
   fp2 Iacc{0.0f, 0.0f};
-  for (int i = 0; i < p.M; ++i) {
-    const size_t o = (base + i) * p.Bpad + b;
-    const float d = p.s32[base + i] * p.dhat[o];
-    const fp2 wn = first ? fp2{d, 0.0f} : padd(ldw_any(p, o), fp2{d, 0.0f});
-    st2(p.w2, o, wn);
-    Iacc = padd(Iacc, pmul(ld2(p.h2, base + i), wn));
+  for (int i0 = 0; i0 < p.M; i0 += kUpd) {
+    const int n = min(kUpd, p.M - i0);
+    float d[kUpd];
+    fp2 w[kUpd];
+#pragma unroll
+    for (int q = 0; q < kUpd; ++q) {
+      if (q < n) {
+        const long o = (long)(i0 + q) * (long)rs;
+        d[q] = dh[o];
+        if (!first) {
+          if (w1) {
+            w[q] = fp2{w1[o], 0.0f};
+          } else {
+            const float2 v = w2[o];
+            w[q] = fp2{v.x, v.y};
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kUpd; ++q) {
+      if (q < n) {
+        const int i = i0 + q;
+        const float dd = p.s32[base + i] * d[q];
+        const fp2 wn = first ? fp2{dd, 0.0f} : padd(w[q], fp2{dd, 0.0f});
+        w2[(long)i * (long)rs] = make_float2(wn.hi, wn.lo);
+        Iacc = padd(Iacc, pmul(ld2(p.h2, base + i), wn));
+      }
+    }
   }
   if (b < p.B) p.I[(size_t)b * p.N + j] = (double)Iacc.hi + (double)Iacc.lo;
 }
