@@ -159,15 +159,23 @@ __device__ __forceinline__ bool epi_sync_or(bool v) {
 
 // Operand stages: each holds tc_sub consecutive 16-wide K chunks, a chunk slot only the KP terms a
 // sweep copies, so there is one full/empty hand-off (wait, fence, commit) per tc_sub chunks; as many
-// stages (2 to 8) as the shared memory beside the three-term vector operand holds.
+// stages (2 to 8) as the shared memory beside the KP-term vector operand holds.  (Five stages of two
+// chunks for a two-term 256-row step ran no faster than two of four: the ring is not what limits
+// the K loop.)
 __host__ __device__ constexpr int tc_sub(int Mt, int KP) { return (Mt == 256 && KP == 3) ? 2 : 4; }
 __host__ __device__ constexpr uint32_t tc_slot(int Mt, int KP) { return (uint32_t)KP * tc::kKC * Mt * 2; }
+__host__ __device__ constexpr int tc_vbytes(int Mt, int KP) { return KP * (tc::kBP / 8) * (int)tc::lbo_b(Mt); }
+// 256-row blocks: each epilogue thread's second 32-column block of the next step's z or right-hand
+// side, copied into shared memory ahead of the accumulator wait
+__host__ __device__ constexpr int tc_prebytes(int Mt) { return Mt == 256 ? tc::kThreads * 32 * 4 : 0; }
+__host__ __device__ constexpr int tc_fixed(int Mt, int KP) { return 2304 + tc_vbytes(Mt, KP) + tc_prebytes(Mt); }
 __host__ __device__ constexpr int tc_stages(int Mt, int KP) {
-  return (232448 - 2304 - (int)(tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt))) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP)) > 8
+  return (232448 - tc_fixed(Mt, KP)) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP)) > 8
              ? 8
-             : (232448 - 2304 - (int)(tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt))) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP));
+             : (232448 - tc_fixed(Mt, KP)) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP));
 }
-static_assert(tc_stages(256, 2) == 2 && tc_stages(256, 3) == 2 && tc_stages(128, 2) == 5 && tc_stages(128, 3) == 3,
+static_assert(tc_stages(256, 1) == 5 && tc_stages(256, 2) == 2 && tc_stages(256, 3) == 2 &&
+                  tc_stages(128, 2) == 6 && tc_stages(128, 3) == 3,
               "stage rings");
 
 // NH = number of 128-row halves of X_j (Mt = 128 NH); KP = number of BF16 terms of the split used
@@ -202,8 +210,10 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
   constexpr uint32_t slot_bytes = tc_slot(Mt, KP);  // one chunk's KP terms in shared memory
   constexpr uint32_t stage_bytes = kSub * slot_bytes;
   static_assert((Mt / KC) % kSub == 0, "a stage must not span two column steps");
-  unsigned char* vb = xs + (size_t)NS * stage_bytes;   // 24 column groups of lbo_b(Mt) bytes: [v0 | v1 | v2]
+  unsigned char* vb = xs + (size_t)NS * stage_bytes;   // 8 KP column groups of lbo_b(Mt) bytes: [v0 | v1 | v2]
   constexpr uint32_t LBO_B = lbo_b(Mt);
+  // [8 float4][kThreads]: thread t's 16-byte piece k at k * kThreads + t (conflict-free reads)
+  float4* pres = reinterpret_cast<float4*>(vb + tc_vbytes(Mt, KP));
 
   constexpr int cps = Mt / KC;  // chunks per step
   const int nsteps = 2 * N - 1;
@@ -407,6 +417,39 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       const bool use_z = !fwd && real;
       const bool use_r = more && nfwd && p.rhs && real;
       float pre[ncb][32];
+      // block 1 (nh == 2): 16-byte cp.async copies into this thread's slice of pres, waited for
+      // after the accumulator wait, so their latency overlaps it
+      auto async_pre1 = [&]() {
+        if (use_z) {
+          const float4* zrow = reinterpret_cast<const float4*>(zp) + (size_t)((cb + 32) / 4) * Mp + i;
+#pragma unroll
+          for (int n = 0; n < 32; n += 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(pres + (n / 4) * kThreads + tid)),
+                         "l"(zrow + (size_t)(n / 4) * Mp)
+                         : "memory");
+        } else if (use_r) {
+          const float* rn = p.rhs + rowoff + 32 + (size_t)Mp * Bpad;
+#pragma unroll
+          for (int n = 0; n < 32; n += 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(pres + (n / 4) * kThreads + tid)),
+                         "l"(rn + n)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      };
+      auto take_pre1 = [&]() {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (use_z || use_r) {
+#pragma unroll
+          for (int n = 0; n < 32; n += 4) {
+            const float4 v4 = pres[(n / 4) * kThreads + tid];
+            pre[ncb - 1][n] = v4.x;
+            pre[ncb - 1][n + 1] = v4.y;
+            pre[ncb - 1][n + 2] = v4.z;
+            pre[ncb - 1][n + 3] = v4.w;
+          }
+        }
+      };
       auto load_pre = [&](int blk) {
         if (use_z) {
           const float4* zrow = reinterpret_cast<const float4*>(zp) + (size_t)((cb + blk * 32) / 4) * Mp + i;
@@ -431,15 +474,18 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
         }
       };
       load_pre(0);
+      if (nh == 2) async_pre1();
       // one thread polls the accumulator barrier; the others wait on the named hardware barrier so
       // that no shared-memory polling competes with the tensor core's operand reads
       bool okd = true;
       if (tid == 32) okd = mbar_spin_bounded(dfull, (unsigned)(s & 1), p.status, wlim, 64);
       if (!okd) atomicExch(fail, 1u);
-      if (epi_sync_or(*fail != 0)) break;
+      if (epi_sync_or(*fail != 0)) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the loop
+        break;
+      }
       fence_after();
-#pragma unroll
-      for (int blk = 1; blk < ncb; ++blk) load_pre(blk);
+      if (nh == 2) take_pre1();
 
       // (1) D of this step per column block (z added in the back substitution), then (2) the next
       // step's input from it, split into BF16 terms; then the next step's MMAs may start
@@ -534,8 +580,8 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
 }
 
 size_t sweep_tc_smem_bytes(int Mt, int KP) {
-  return 256 + 8 * 64 * 4 + (size_t)tc_stages(Mt, KP) * tc_sub(Mt, KP) * tc_slot(Mt, KP) +
-         (size_t)tc::kParts * (tc::kBP / 8) * tc::lbo_b(Mt);
+  return 256 + 8 * 64 * 4 + (size_t)tc_stages(Mt, KP) * tc_sub(Mt, KP) * tc_slot(Mt, KP) + tc_vbytes(Mt, KP) +
+         tc_prebytes(Mt);
 }
 
 bool sweep_tc_supported(int Mp) { return Mp <= 256; }
