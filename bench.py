@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-factor-rates", action="store_true", help="skip the standalone factor timings")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate workload nested in the default line")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch size (profiling runs)")
+    ap.add_argument("--algorithm", default="thomas", choices=["thomas", "cr"],
+                    help="factor and substitution of the pipelined step: block Thomas or block cyclic reduction "
+                         "(tensor-core products)")
     ap.add_argument("--epochs", type=int, default=24, help="surrogate workload: training epochs")
     ap.add_argument("--line-passes", type=int, default=2, help="surrogate workload: line-model passes")
     return ap.parse_args()
@@ -209,6 +212,10 @@ def run_xbar(args):
     # the mixed path) runs on SMs the solve leaves free.  Both maps hold the workload's conductances.
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     xbs = [xbar.Crossbar.assemble(Gd, *R, stream=s) for s in streams]
+    for xb_ in xbs:
+        xb_.set_option("algorithm", args.algorithm)
+        if args.algorithm == "cr":
+            xb_.set_option("cr_products", 1)
     Is = [torch.zeros((B, N), dtype=torch.float64, device="cuda") for _ in range(2)]
     I64s = [torch.zeros((B, N), dtype=torch.float64, device="cuda") for _ in range(2)]
     info_box = {}
@@ -411,7 +418,7 @@ def run_xbar(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16x3 tensor products) + f32-pair refinement", "data": "synthetic",
         "config": {"workload": args.workload + (f"_B{B}" if args.batch else ""), "M": M, "N": N, "B": B,
                    "R_s": R[0], "R_w": R[1], "R_b": R[2], "R_sense": R[3], "precision": "fp32 factor, sweeps on BF16 tensor cores (three-term split, fp32 accumulation), float-pair (~48-bit) residual/update", "tol": TOL,
-                   "step": "set_conductances + factor + solve (all refinement)",
+                   "step": "set_conductances + factor + solve (all refinement)", "algorithm": args.algorithm,
                    "schedule": "two maps in flight: each step sets and factors the next map on a second "
                                "stream while this map's batch is solved (FP64 baseline and e2e the same)",
                    "l2": "working set per step (>6 GB) exceeds the 129 MB L2", "parallelism": f"replicas{world}"},

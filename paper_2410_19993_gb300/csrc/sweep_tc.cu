@@ -388,22 +388,28 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       }
     release_v();
 
+    // warm L2 with the global operands step s2's epilogue reads before its accumulator wait: z of
+    // step s2 (back substitution) or the right-hand side of the column after it (forward).  Issued
+    // as soon as step s2 - 1 has released its vector, so the copies overlap that step's stores.
+    auto warm_l2 = [&](int s2) {
+      const bool fwd2 = s2 < N;
+      const int j2 = fwd2 ? s2 : 2 * N - 2 - s2;
+      const float* zp2 = p.z + ((size_t)j2 * (Bpad / BP) + blockIdx.x) * (size_t)Mp * BP;
+      const int i0 = i - lane + (lane & 3) * 8;  // this lane's quarter of the warp's 32 rows
+      for (int blk = 0; blk < ncb; ++blk) {
+        if (!fwd2 && i0 < Mp)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(zp2 + ((size_t)((cb + blk * 32) / 4 + (lane >> 2)) * Mp + i0) * 4));
+        if (real && s2 + 1 < N && p.rhs)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + ((size_t)(j2 + 1) * Mp + i) * Bpad + b0 + cb + blk * 32));
+      }
+    };
+    warm_l2(0);
     float local_max = 0.0f;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < N;
       const int j = fwd ? s : 2 * N - 2 - s;
       const bool nfwd = s + 1 < N;
-      // warm L2 with the global operands this step's epilogue will read
       float* zp = p.z + ((size_t)j * (Bpad / BP) + blockIdx.x) * (size_t)Mp * BP;  // z panel of step j
-      {
-        const int i0 = i - lane + (lane & 3) * 8;  // this lane's quarter of the warp's 32 rows
-        for (int blk = 0; blk < ncb; ++blk) {
-          if (!fwd && i0 < Mp)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(zp + ((size_t)((cb + blk * 32) / 4 + (lane >> 2)) * Mp + i0) * 4));
-          if (real && nfwd && p.rhs)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.rhs + ((size_t)(j + 1) * Mp + i) * Bpad + b0 + cb + blk * 32));
-        }
-      }
       const float ej = real ? (nfwd ? p.e[(size_t)j * Mp + i] : (j > 0 ? p.e[(size_t)(j - 1) * Mp + i] : 0.0f))
                             : 0.0f;
       const float hj = real ? p.hs[(size_t)j * Mp + i] : 0.0f;
@@ -507,6 +513,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
           }
         }
         release_v();
+        warm_l2(s + 1);
       }
       // (3) while the next step's MMAs run: z (forward), w and the current (back substitution)
       float dots[ncb];
