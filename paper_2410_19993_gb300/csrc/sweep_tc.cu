@@ -165,9 +165,10 @@ __device__ __forceinline__ bool epi_sync_or(bool v) {
 __host__ __device__ constexpr int tc_sub(int Mt, int KP) { return (Mt == 256 && KP == 3) ? 2 : 4; }
 __host__ __device__ constexpr uint32_t tc_slot(int Mt, int KP) { return (uint32_t)KP * tc::kKC * Mt * 2; }
 __host__ __device__ constexpr int tc_vbytes(int Mt, int KP) { return KP * (tc::kBP / 8) * (int)tc::lbo_b(Mt); }
-// 256-row blocks: each epilogue thread's second 32-column block of the next step's z or right-hand
-// side, copied into shared memory ahead of the accumulator wait
-__host__ __device__ constexpr int tc_prebytes(int Mt) { return Mt == 256 ? tc::kThreads * 32 * 4 : 0; }
+// 32 floats per epilogue thread: with 256-row blocks, the second 32-column block of the next step's
+// z or right-hand side, copied in ahead of the accumulator wait; in every sweep, the staging of the
+// w tiles (4 KB per warp) between those copies
+__host__ __device__ constexpr int tc_prebytes(int Mt) { return tc::kThreads * 32 * 4; }
 __host__ __device__ constexpr int tc_fixed(int Mt, int KP) { return 2304 + tc_vbytes(Mt, KP) + tc_prebytes(Mt); }
 __host__ __device__ constexpr int tc_stages(int Mt, int KP) {
   return (232448 - tc_fixed(Mt, KP)) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP)) > 8
@@ -175,7 +176,7 @@ __host__ __device__ constexpr int tc_stages(int Mt, int KP) {
              : (232448 - tc_fixed(Mt, KP)) / (int)(tc_sub(Mt, KP) * tc_slot(Mt, KP));
 }
 static_assert(tc_stages(256, 1) == 5 && tc_stages(256, 2) == 2 && tc_stages(256, 3) == 2 &&
-                  tc_stages(128, 2) == 6 && tc_stages(128, 3) == 3,
+                  tc_stages(128, 2) == 5 && tc_stages(128, 3) == 3,
               "stage rings");
 
 // NH = number of 128-row halves of X_j (Mt = 128 NH); KP = number of BF16 terms of the split used
@@ -404,6 +405,28 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       }
     };
     warm_l2(0);
+    // the warp's 32 x 32 tile v (lane = row) times sc to rows (i - lane) + r of dst (row stride
+    // Bpad), r < 32, columns 0..31, staged in pres so that each store instruction writes 4 whole
+    // rows.  Float4 q of row r goes to pres[(r & 7) kThreads + 32 warp + ((r & 24) | ((r + q) & 7))]:
+    // only the pieces of this warp's own threads' copies (each thread has consumed its own, and
+    // the next step's copies follow in program order), so no other warp shares the slice; the skew
+    // keeps both the row writes and the chunk reads free of bank conflicts.
+    float4* wst = pres + 32 * warp;
+    auto store_rows = [&](float* dst, const float (&v)[32], float sc) {
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        wst[(lane & 7) * kThreads + ((lane & 24) | ((lane + q) & 7))] =
+            make_float4(sc * v[4 * q], sc * v[4 * q + 1], sc * v[4 * q + 2], sc * v[4 * q + 3]);
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int r = 4 * m + (lane >> 3), q = lane & 7;
+        const float4 x = wst[(r & 7) * kThreads + ((r & 24) | ((r + q) & 7))];
+        if (i - lane + r < Mp) *reinterpret_cast<float4*>(dst + (size_t)r * Bpad + 4 * q) = x;
+      }
+      __syncwarp();
+    };
     float local_max = 0.0f;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < N;
@@ -417,6 +440,9 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       const size_t rowoff = ((size_t)j * Mp + (real ? i : 0)) * Bpad + b0 + cb;
       const bool have_w = !fwd || s == N - 1;
       const bool more = s + 1 < nsteps;
+      // the current this step adds to, read now so that its latency overlaps the accumulator wait
+      double Iold = 0.0;
+      if (have_w && p.accumulate && tid < BP && b0 + tid < p.B) Iold = p.I[(size_t)(b0 + tid) * N + j];
       // the next input's operands that do not depend on D -- z of this step (back substitution) or
       // the next column's right-hand side (forward) -- are loaded before the wait: column block 0
       // now, block 1 right after it, so their latency leaves the step's critical path
@@ -519,7 +545,6 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
       float dots[ncb];
 #pragma unroll
       for (int blk = 0; blk < ncb; ++blk) {
-        const size_t o = rowoff + blk * 32;
         float a[32];  // this step's D again (its accumulator set is not written until step s + 2)
         tmem_ld32(tstep + blk * 32, a);
         if (use_z)
@@ -532,16 +557,12 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
             zrow[(size_t)(n / 4) * Mp] = make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
         }
         if (have_w) {
-          if (p.w && real)
-#pragma unroll
-            for (int n = 0; n < 32; n += 4)
-              *reinterpret_cast<float4*>(p.w + o + n) =
-                  make_float4(a[n], a[n + 1], a[n + 2], a[n + 3]);
-          if (p.w1out && real)  // refinement state s o w (FP32; the float pairs' low part is 0)
-#pragma unroll
-            for (int n = 0; n < 32; n += 4)
-              *reinterpret_cast<float4*>(p.w1out + o + n) =
-                  make_float4(sj * a[n], sj * a[n + 1], sj * a[n + 2], sj * a[n + 3]);
+          // w (or the refinement state s o w, FP32: the float pairs' low part is 0) of this block's
+          // 32 rows x 32 columns, written as whole 128-byte row segments through the warp's slice of
+          // pres (free until the next step's copies, which follow the epi_sync below)
+          if (p.w || p.w1out)
+            store_rows((p.w ? p.w : p.w1out) + ((size_t)j * Mp + (i - lane)) * Bpad + b0 + cb + blk * 32, a,
+                       p.w ? 1.0f : sj);
 #pragma unroll
           for (int n = 0; n < 32; ++n) a[n] *= hj;
           dots[blk] = transpose_sum32(a, lane);
@@ -565,7 +586,7 @@ __global__ void __launch_bounds__(tc::kThreads + 64, 1)
           const double dI = (double)sum;
           if (!isfinite(dI)) set_status(p.status, XBAR_DEV_NONFINITE);
           if (p.accumulate) {
-            const double In = *Ip + dI;
+            const double In = Iold + dI;
             *Ip = In;
             local_max = fmaxf(local_max, (float)(fabs(dI) / fmax(fabs(In), 1e-300)));
           } else {
