@@ -232,7 +232,13 @@ def run_xbar(args):
     def step_pipelined(V_in, outs, solve_kwargs):
         k = pipe["k"]
         cur, nxt = xbs[k % 2], xbs[(k + 1) % 2]
-        nxt.set_conductances(Gd)  # map k+1: set, assembled and factored on its own stream ...
+        nxt.set_conductances(Gd)  # map k+1: set and assembled on its own stream, then factored ...
+        # map k's solve starts once that assembly is done, with the factor already queued ahead of
+        # it: the factor's 16-block cluster then takes its SMs before the solve's sweep fills them
+        # (a cluster needs 16 free SMs of one GPC, which a running sweep rarely leaves)
+        assembled = torch.cuda.Event()
+        assembled.record(streams[(k + 1) % 2])
+        streams[k % 2].wait_event(assembled)
         nxt.factor(pipe["prec"])
         _, info = cur.solve(V_in, outs[k % 2], **solve_kwargs)  # ... beside map k's solve
         pipe["solved"].add((id(outs), k % 2))

@@ -181,8 +181,10 @@ xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value);
 /*
  * xbar_set_conductances -- load a new conductance map G into the handle (same
  * M, N and resistances; host or device pointer) without reallocating.  The
- * handle becomes unfactored; as after xbar_assemble, the column elimination
- * data are formed by the next xbar_factor.  A host G is validated before the
+ * handle becomes unfactored.  The column elimination data (Sec. II-A) are formed
+ * here, asynchronously on the handle's stream, so that a factor queued after
+ * this call starts at once; a caller pipelining maps over two streams can record
+ * an event after this call and hold the other stream on it.  A host G is validated before the
  * call returns.  A device G is read and validated on the device, asynchronously
  * on the handle's stream (the call does not wait for that stream): a negative or
  * non-finite entry is reported as XBAR_EINVAL by the next call that reads the

@@ -1152,8 +1152,12 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
   {
     // a device map is validated by the transposing kernel itself (status word, reported by the
     // next call that reads it), so the host does not wait for the stream here
-    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 1);
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 4);
     XB_CUDA(launch_store_g(m, Gd, gdev ? h->status : nullptr, h->st));
+    // the elimination data at once, so that work queued behind this call on the stream (a factor)
+    // finds it ready; xbar_factor assembles only when this has not happened
+    XB_CUDA(launch_assemble(m, h->st));
+    h->assembled = 1;
   }
   if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
   return XBAR_OK;

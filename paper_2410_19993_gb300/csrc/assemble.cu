@@ -30,27 +30,68 @@ __global__ void asm_gc_kernel(MapDev m, const double* __restrict__ G, unsigned* 
   m.Gc[(size_t)j * m.Mp + i] = g;
 }
 
-// One thread per bit line j: the chain recurrences of T_j (sequential in i), from Gc.
+// The pivot recurrences of T_j are chains of linear-fractional maps, x -> g_b (G + x) / (G + x + g_b)
+// (top-down: alpha_i from alpha_{i-1} with G = G_{i-1}; bottom-up: beta_i from beta_{i+1} with
+// G = G_{i+1}).  A map is the 2 x 2 matrix [[g_b, g_b G], [1, G + g_b]] acting on (x, 1), and a chain of
+// them is the matrix product: all entries are >= 0, so products keep full relative accuracy.  One warp
+// takes a bit line: each lane composes the maps of its segment of rows, a warp scan composes the
+// segments, and each lane then walks only its own rows from the value the scan gives at their start.
+struct Mob {
+  double a, b, c, d;  // x -> (a x + b) / (c x + d)
+};
+__device__ __forceinline__ Mob mob_id() { return {1.0, 0.0, 0.0, 1.0}; }
+__device__ __forceinline__ Mob mob_step(double G, double gb) { return {gb, gb * G, 1.0, G + gb}; }
+// X o Y, rescaled by a power of two (exact) so that the largest entry is in [1/2, 1)
+__device__ __forceinline__ Mob mob_mul(const Mob& X, const Mob& Y) {
+  const Mob r{X.a * Y.a + X.b * Y.c, X.a * Y.b + X.b * Y.d, X.c * Y.a + X.d * Y.c, X.c * Y.b + X.d * Y.d};
+  int e;
+  frexp(fmax(fmax(r.a, r.b), fmax(r.c, r.d)), &e);
+  return {ldexp(r.a, -e), ldexp(r.b, -e), ldexp(r.c, -e), ldexp(r.d, -e)};
+}
+__device__ __forceinline__ double mob_apply(const Mob& X, double x) { return (X.a * x + X.b) / (X.c * x + X.d); }
+__device__ __forceinline__ Mob shfl_up_mob(const Mob& X, int k) {
+  return {__shfl_up_sync(0xffffffffu, X.a, k), __shfl_up_sync(0xffffffffu, X.b, k),
+          __shfl_up_sync(0xffffffffu, X.c, k), __shfl_up_sync(0xffffffffu, X.d, k)};
+}
+__device__ __forceinline__ Mob shfl_down_mob(const Mob& X, int k) {
+  return {__shfl_down_sync(0xffffffffu, X.a, k), __shfl_down_sync(0xffffffffu, X.b, k),
+          __shfl_down_sync(0xffffffffu, X.c, k), __shfl_down_sync(0xffffffffu, X.d, k)};
+}
+
+// One warp per bit line j (blocks of 4 warps); lane L owns rows [L K, L K + K), K = ceil(M / 32).
 __global__ void asm_columns_kernel(MapDev m) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m.N) return;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= m.N) return;  // whole warps leave together
   const int M = m.M, N = m.N, Mp = m.Mp;
   const double gs = m.gs, gw = m.gw, gb = m.gb, go = m.go;
-  double* Gc = m.Gc + (size_t)j * Mp;
+  const double* Gc = m.Gc + (size_t)j * Mp;
   double* dW = m.dW + (size_t)j * Mp;
   double* tha = m.tha + (size_t)j * Mp;
   double* thc = m.thc + (size_t)j * Mp;
   double* tdiag = m.tdiag + (size_t)j * Mp;
   double* rho = m.rho + (size_t)j * Mp;
   double* h = m.h + (size_t)j * Mp;
+  const int K = (M + 31) / 32;
+  const int i0 = min(lane * K, M), i1 = min(i0 + K, M);
 
   // top-down: pivots d-_i = G_i + alpha_i + (i < M-1 ? g_b : g_o),
   //           alpha_0 = 0, alpha_i = g_b t / (t + g_b), t = G_{i-1} + alpha_{i-1}
-  double alpha = 0.0, gprev = 0.0;
-  for (int i = 0; i < M; ++i) {
+  // this lane's maps produce alpha_i for i0 < i <= i1 (i <= M - 1)
+  Mob P = mob_id();
+  for (int i = i0 + 1; i <= i1 && i <= M - 1; ++i) P = mob_mul(mob_step(Gc[i - 1], gb), P);
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {  // inclusive scan: P = S_L o S_{L-1} o ... o S_0
+    const Mob Y = shfl_up_mob(P, k);
+    if (lane >= k) P = mob_mul(P, Y);
+  }
+  Mob E = shfl_up_mob(P, 1);  // the maps before this lane's rows
+  if (lane == 0) E = mob_id();
+  double alpha = mob_apply(E, 0.0);  // alpha_{i0}
+  for (int i = i0; i < i1; ++i) {
     const double g = Gc[i];
-    if (i > 0) {
-      const double t = gprev + alpha;
+    if (i > i0) {
+      const double t = Gc[i - 1] + alpha;
       alpha = gb * t / (t + gb);
     }
     const double dminus = g + alpha + (i < M - 1 ? gb : go);
@@ -58,28 +99,50 @@ __global__ void asm_columns_kernel(MapDev m) {
     dW[i] = g + (j == 0 ? gs : gw) + (j < N - 1 ? gw : 0.0);
     tha[i] = g * inv;
     thc[i] = gb * inv;
-    tdiag[i] = alpha;  // kept until the bottom-up pass
-    gprev = g;
+    tdiag[i] = alpha;  // kept until the bottom-up pass (same thread)
   }
   // bottom-up: pivots d+_i = G_i + beta_i + (i > 0 ? g_b : 0),
   //            beta_{M-1} = g_o, beta_i = g_b t / (t + g_b), t = G_{i+1} + beta_{i+1}
-  // diag(T^-1)_i = 1 / (G_i + alpha_i + beta_i);  T^-1_{i,k} = T^-1_{i,k-1} * g_b / d+_k  (k > i)
-  double beta = go, gnext = 0.0, q = 1.0;
-  for (int i = M - 1; i >= 0; --i) {
+  // this lane's maps produce beta_i for i0 <= i < i1 (i <= M - 2)
+  Mob Q = mob_id();
+  for (int i = i0; i < min(i1, M - 1); ++i) Q = mob_mul(Q, mob_step(Gc[i + 1], gb));  // g_i0 o ... o g_top
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {  // inclusive suffix scan: Q = T_L o T_{L+1} o ... o T_31
+    const Mob Y = shfl_down_mob(Q, k);
+    if (lane + k < 32) Q = mob_mul(Q, Y);
+  }
+  Mob U = shfl_down_mob(Q, 1);  // the maps below this lane's rows
+  if (lane == 31) U = mob_id();
+  // diag(T^-1)_i = 1 / (G_i + alpha_i + beta_i);  rho_i = g_b / d+_i;  h_i = g_o G_i diag(T^-1)_i q_i,
+  // q_i = prod_{k=i+1}^{M-1} rho_k
+  double beta = mob_apply(U, go);  // beta_{i1} (g_o when i1 >= M - 1)
+  double rp = 1.0;                 // product of rho over this lane's rows
+  for (int i = i1 - 1; i >= i0; --i) {
     const double g = Gc[i];
     if (i < M - 1) {
-      const double t = gnext + beta;
+      const double t = Gc[i + 1] + beta;
       beta = gb * t / (t + gb);
+    } else {
+      beta = go;
     }
     const double dplus = g + beta + (i > 0 ? gb : 0.0);
-    const double td = 1.0 / (g + tdiag[i] + beta);
-    tdiag[i] = td;
-    if (i < M - 1) q *= rho[i + 1];  // q = prod_{k=i+1}^{M-1} rho_k
+    tdiag[i] = 1.0 / (g + tdiag[i] + beta);
     rho[i] = gb / dplus;
-    h[i] = go * g * td * q;
-    gnext = g;
+    rp *= rho[i];
   }
-  for (int i = M; i < Mp; ++i) {
+  double qs = rp;  // suffix product over lanes L .. 31
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    const double y = __shfl_down_sync(0xffffffffu, qs, k);
+    if (lane + k < 32) qs *= y;
+  }
+  double q = __shfl_down_sync(0xffffffffu, qs, 1);  // rows below this lane's
+  if (lane == 31) q = 1.0;
+  for (int i = i1 - 1; i >= i0; --i) {
+    if (i < i1 - 1) q *= rho[i + 1];
+    h[i] = go * Gc[i] * tdiag[i] * q;
+  }
+  for (int i = M + lane; i < Mp; i += 32) {
     dW[i] = 1.0;
     tha[i] = 0.0;
     thc[i] = 0.0;
@@ -161,7 +224,7 @@ cudaError_t launch_store_g(const MapDev& m, const double* G_dev, unsigned* statu
 }
 
 cudaError_t launch_assemble(const MapDev& m, cudaStream_t st) {
-  asm_columns_kernel<<<(m.N + 63) / 64, 64, 0, st>>>(m);
+  asm_columns_kernel<<<(m.N + 3) / 4, 128, 0, st>>>(m);
   dim3 g2((m.Mp + 127) / 128, m.N);
   asm_scale_kernel<<<g2, 128, 0, st>>>(m);
   asm_coff_kernel<<<g2, 128, 0, st>>>(m);
