@@ -55,7 +55,10 @@ constexpr int kThreads = 256;
 // node groups of 8 are 128 bytes apart, column groups (Mt/8)*128 bytes apart
 __host__ __device__ constexpr uint32_t lbo_b(int Mt) { return (uint32_t)(Mt / 8) * 128; }  // column-group stride
 // tensor-memory columns for NH halves of KP * 64 columns (allocations are powers of two >= 32)
-// two accumulators (steps alternate) of NH x 64 columns each
+// two accumulators (steps alternate) of NH x 64 columns each.  (Issuing A_0 [v_0 | v_1] as one
+// N = 128 product, with the epilogue adding the two 64-column halves, reads A_0 once per K step
+// instead of twice, but the extra accumulator reads on the epilogue's critical path cost more:
+// measured 5% slower per step.)
 __host__ __device__ constexpr uint32_t tmem_cols(int NH) { return NH == 1 ? 128u : 256u; }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
