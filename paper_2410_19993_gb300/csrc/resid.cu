@@ -265,7 +265,7 @@ __device__ __forceinline__ void back_walk(const ResidParams& p, const ColCoef& c
 }
 
 template <bool kW1>
-__global__ void __launch_bounds__(128, 7) resid_kernel(ResidParams p) {
+__global__ void __launch_bounds__(128, 8) resid_kernel(ResidParams p) {
   if (p.skip && *p.skip) return;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
