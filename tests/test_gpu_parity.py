@@ -207,3 +207,29 @@ def test_not_converged_is_reported():
     assert st == xbar.XBAR_ENOTCONV
     assert info["iters"] == 1 and info["max_rel_dI"] > 0
     xb.destroy()
+
+
+# ---------------------------------------------------------------------------------------------
+# long bit-line chains: the assembly's pivot recurrences run as warp scans over 32 row segments
+# (uneven when 32 does not divide M); the mirrored crossbar of a wide map has long chains too
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("M,N,B,orientation", [(1024, 3, 6, "columns"), (1000, 2, 5, "columns"),
+                                               (777, 4, 3, "columns"), (65, 1, 4, "columns"),
+                                               (3, 640, 4, "rows"), (2, 999, 3, "rows")])
+def test_long_chains_against_oracle(M, N, B, orientation):
+    G, V = case(M, N, B, None, seed=M + 7 * N)
+    R = (1.0, 2.5, 1.5, 10.0)
+    ref = oracle.solve(M, N, G, *R, V, voltages=True)
+    Gt, Vt = _dev(G), _dev(V)
+    I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    vW = torch.zeros((B, M, N), dtype=torch.float64, device="cuda")
+    vB = torch.zeros((B, M, N), dtype=torch.float64, device="cuda")
+    xb = xbar.Crossbar.assemble(Gt, *R)
+    xb.set_option("orientation", orientation)
+    xb.factor("fp64")
+    xb.solve(Vt, I, vW, vB)
+    xb.sync()
+    xb.destroy()
+    assert rel_err(I.cpu().numpy(), ref["I"]) <= FP64_BAR
+    assert np.max(np.abs(vW.cpu().numpy() - ref["vWL"])) <= FP64_BAR
+    assert np.max(np.abs(vB.cpu().numpy() - ref["vBL"])) <= FP64_BAR

@@ -1,0 +1,74 @@
+"""Repeatability: the same batch solved again on the same handle gives the same bits.
+
+The tensor-core sweep's epilogue warps share one shared-memory slab (copies of the next operand
+block, then the staging of the w tiles), and several other kernels split work across warps.  A
+race between warps would make results depend on warp timing, which the element-wise bars of the
+parity tests can miss when the difference is small.  Every output here must be bit-identical
+across repeated solves: currents, and both node-voltage fields where they are requested.
+"""
+import numpy as np
+import pytest
+
+from paper_2410_19993_gb300 import inputs, xbar
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+R = (1.0, 1.0, 1.0, 10.0)
+
+
+def _repeat(M, N, B, precision, reps, voltages, seed=11):
+    G, V = inputs.crossbar(M, N, B, seed=seed)
+    Gd, Vd = torch.from_numpy(G).cuda(), torch.from_numpy(V).cuda()
+    xb = xbar.Crossbar.assemble(Gd, *R)
+    xb.factor(precision)
+    outs = []
+    for _ in range(reps):
+        I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+        vW = torch.zeros((B, M, N), dtype=torch.float64, device="cuda") if voltages else None
+        vB = torch.zeros((B, M, N), dtype=torch.float64, device="cuda") if voltages else None
+        xb.solve(Vd, I, vW, vB, tol=1e-9, max_iter=10)
+        xb.sync()
+        outs.append([t for t in (I, vW, vB) if t is not None])
+    xb.destroy()
+    return outs
+
+
+@pytest.mark.parametrize("M,N,B,voltages", [(256, 256, 1024, True), (256, 256, 8192, False),
+                                             (128, 64, 2048, True), (200, 33, 640, True)])
+def test_repeated_mixed_solves_bit_identical(M, N, B, voltages):
+    outs = _repeat(M, N, B, "fp32_ir", 4, voltages)
+    for k, o in enumerate(outs[1:], 1):
+        for name, a, b in zip(("I", "vWL", "vBL"), o, outs[0]):
+            assert torch.equal(a, b), f"solve {k}, {name}: max |diff| = {float((a - b).abs().max())}"
+
+
+def test_repeated_fp64_solves_bit_identical():
+    outs = _repeat(256, 256, 512, "fp64", 3, True)
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert torch.equal(a, b)
+
+
+def test_set_conductances_then_factor_matches_fresh_handle():
+    """xbar_set_conductances assembles at once; a handle reused that way must give exactly what a
+    fresh handle of the same map gives."""
+    M, N, B = 256, 256, 1024
+    G1, V = inputs.crossbar(M, N, B, seed=21)
+    G2, _ = inputs.crossbar(M, N, 1, seed=22)
+    Vd = torch.from_numpy(V).cuda()
+    fresh = xbar.Crossbar.assemble(torch.from_numpy(G2).cuda(), *R)
+    fresh.factor("fp32_ir")
+    I_fresh = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    fresh.solve(Vd, I_fresh, tol=1e-9)
+    fresh.sync()
+    fresh.destroy()
+    reused = xbar.Crossbar.assemble(torch.from_numpy(G1).cuda(), *R)
+    reused.factor("fp32_ir")
+    reused.set_conductances(torch.from_numpy(G2).cuda())
+    reused.factor("fp32_ir")
+    I = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+    reused.solve(Vd, I, tol=1e-9)
+    reused.sync()
+    reused.destroy()
+    assert torch.equal(I, I_fresh)
