@@ -213,6 +213,7 @@ def run_xbar(args):
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     xbs = [xbar.Crossbar.assemble(Gd, *R, stream=s) for s in streams]
     for xb_ in xbs:
+        xb_.set_option("eager_assembly", 1)  # set_conductances assembles: see step_pipelined
         xb_.set_option("algorithm", args.algorithm)
         if args.algorithm == "cr":
             xb_.set_option("cr_products", 1)
@@ -232,7 +233,7 @@ def run_xbar(args):
     def step_pipelined(V_in, outs, solve_kwargs):
         k = pipe["k"]
         cur, nxt = xbs[k % 2], xbs[(k + 1) % 2]
-        nxt.set_conductances(Gd)  # map k+1: set and assembled on its own stream, then factored ...
+        nxt.set_conductances(Gd)  # map k+1: set and (eager_assembly) assembled on its own stream ...
         # map k's solve starts once that assembly is done, with the factor already queued ahead of
         # it: the factor's 16-block cluster then takes its SMs before the solve's sweep fills them
         # (a cluster needs 16 free SMs of one GPC, which a running sweep rarely leaves)

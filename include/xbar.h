@@ -156,7 +156,7 @@ typedef enum {
                                  return; the next call that reads the handle's device status
                                  returns XBAR_ETIMEOUT and the results of that work are invalid.
                                  Synchronises the handle's stream. */
-  XBAR_OPT_ORIENTATION = 5    /* XBAR_FP64 factors: 0 = blocks over the N columns (M x M blocks,
+  XBAR_OPT_ORIENTATION = 5,   /* XBAR_FP64 factors: 0 = blocks over the N columns (M x M blocks,
                                  bit lines eliminated inside each column; Sec. II-B ordering),
                                  1 = blocks over the M rows (N x N blocks, word lines eliminated
                                  inside each row: the same system written for the mirrored
@@ -171,6 +171,12 @@ typedef enum {
                                  (the refinement then runs on the mirrored crossbar); the tile
                                  batch (xbar_batch_run) blocks over rows in XBAR_FP64 only.  Takes
                                  effect at the next xbar_factor. */
+  XBAR_OPT_EAGER_ASSEMBLY = 6 /* 1 = xbar_set_conductances also forms the column elimination data
+                                 (Sec. II-A), on the handle's stream, so that a factor queued
+                                 behind it starts at once (a caller pipelining maps over two
+                                 streams records an event after the call); 0 or -1 (default) =
+                                 the next xbar_factor forms them, and callers that need only the
+                                 map (the surrogate) never pay for them. */
 } xbar_option;
 
 /* Select a kernel variant for later xbar_factor / xbar_solve calls (value -1, 0 or 1; a
@@ -181,10 +187,9 @@ xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value);
 /*
  * xbar_set_conductances -- load a new conductance map G into the handle (same
  * M, N and resistances; host or device pointer) without reallocating.  The
- * handle becomes unfactored.  The column elimination data (Sec. II-A) are formed
- * here, asynchronously on the handle's stream, so that a factor queued after
- * this call starts at once; a caller pipelining maps over two streams can record
- * an event after this call and hold the other stream on it.  A host G is validated before the
+ * handle becomes unfactored; as after xbar_assemble, the column elimination data
+ * are formed by the next xbar_factor, or here, asynchronously on the handle's
+ * stream, when XBAR_OPT_EAGER_ASSEMBLY is 1.  A host G is validated before the
  * call returns.  A device G is read and validated on the device, asynchronously
  * on the handle's stream (the call does not wait for that stream): a negative or
  * non-finite entry is reported as XBAR_EINVAL by the next call that reads the

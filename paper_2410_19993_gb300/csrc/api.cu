@@ -676,6 +676,7 @@ extern "C" xbar_status xbar_set_option(xbar_t h, xbar_option opt, int value) {
     case XBAR_OPT_ALGORITHM: h->opt.algo = value; break;
     case XBAR_OPT_CR_PRODUCTS: h->opt.cr_tensor = value; break;
     case XBAR_OPT_ORIENTATION: h->opt.orient = value; break;
+    case XBAR_OPT_EAGER_ASSEMBLY: h->opt.eager_asm = value; break;
     default: return fail(XBAR_EINVAL, "unknown option %d", (int)opt);
   }
   return XBAR_OK;
@@ -1152,12 +1153,13 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
   {
     // a device map is validated by the transposing kernel itself (status word, reported by the
     // next call that reads it), so the host does not wait for the stream here
-    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, 4);
+    const bool eager = h->opt.eager_asm == 1;
+    PhaseScope ps(h, XBAR_PHASE_ASSEMBLE, eager ? 4 : 1);
     XB_CUDA(launch_store_g(m, Gd, gdev ? h->status : nullptr, h->st));
-    // the elimination data at once, so that work queued behind this call on the stream (a factor)
-    // finds it ready; xbar_factor assembles only when this has not happened
-    XB_CUDA(launch_assemble(m, h->st));
-    h->assembled = 1;
+    if (eager) {  // the elimination data at once, so that a factor queued behind this call starts
+      XB_CUDA(launch_assemble(m, h->st));
+      h->assembled = 1;
+    }
   }
   if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
   return XBAR_OK;

@@ -97,6 +97,7 @@ struct xbar_opts {
   int algo = -1;    // 0 = block Thomas, 1 = block cyclic reduction
   int cr_tensor = -1;  // cyclic reduction, FP32 products: 0 = CUDA cores, 1 = tensor cores
   int orient = -1;  // FP64 factors: 0 = column blocks, 1 = row blocks (mirrored crossbar), -1 = rows when 2N <= M
+  int eager_asm = -1;  // 1 = xbar_set_conductances also assembles; otherwise the next factor does
 };
 
 struct xbar_s {

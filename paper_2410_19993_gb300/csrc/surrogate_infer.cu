@@ -7,15 +7,16 @@
 // and the prediction I = I_line + I_ideal (mu + sigma n0) with the relative error estimate
 // c sigma exp(n1) |I_ideal| / |I|; flag[b] = 1 when an estimate of vector b is above the bound.
 //
-// Persistent blocks (one per SM, 128 threads): W2 (256 x 256 BF16, 128 KB), pre-tiled in global
+// Persistent blocks (one per SM, 512 threads: four per tile row, each owning a quarter of the
+// 256 hidden columns): W2 (256 x 256 BF16, 128 KB), pre-tiled in global
 // memory in the B operand's layout whenever the weights change, is copied once into shared memory.  A tile is 128 rows = 8 vectors x 16 bit lines, so its operand
 // h1 needs only 16 rows of P and 8 rows of Q (24 KB): they are copied into shared memory with
 // cp.async while the previous tile's epilogue runs, and the threads build h1 (64 KB) from them
 // (thread = row, a warp's 16-byte stores cover 32 consecutive rows: bank-conflict free).  One
 // thread issues 16 MMAs (M = 128, N = 256, K = 16) into one of two 256-column tensor-memory
 // accumulators; while the tensor core works on tile t, the threads drain tile t-1's accumulator
-// (tcgen05.ld), apply b2, ReLU and the BF16 rounding of h2, reduce against W3 and write the
-// prediction.  Every wait is bounded; on expiry the block records XBAR_DEV_TIMEOUT, waits
+// (tcgen05.ld), apply b2, ReLU and the BF16 rounding of h2, reduce against W3 (four partial sums
+// per row, combined through shared memory) and write the prediction.  Every wait is bounded; on expiry the block records XBAR_DEV_TIMEOUT, waits
 // (bounded) for its own MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -32,7 +33,7 @@ namespace si {
 
 constexpr int kH = 256;         // hidden width (K and N of the product)
 constexpr int kRows = 128;      // rows per tile (MMA M)
-constexpr int kThreads = 128;   // thread = tile row
+constexpr int kThreads = 512;   // tile row m = tid % 128, hidden-column quarter tid / 128
 constexpr uint32_t kLA = (kRows / 8) * 128;  // A: K-direction stride between core matrices (2 KB)
 constexpr uint32_t kLB = (kH / 8) * 128;     // B: same for 256 rows (4 KB)
 constexpr uint32_t kBBytes = (kH / 8) * kLB;    // 128 KB
@@ -40,7 +41,8 @@ constexpr uint32_t kABytes = (kH / 8) * kLA;    // 64 KB
 constexpr int kTJ = 16, kTB = kRows / kTJ;      // a tile: kTB vectors x kTJ bit lines
 constexpr int kPPitch = kH + 4;                 // P rows in shared memory (bank offset 4 per row)
 constexpr size_t kPBytes = (size_t)kTJ * kPPitch * 4, kQBytes = (size_t)kTB * kH * 4;
-constexpr size_t kSmem = 1024 + kBBytes + kABytes + (size_t)(2 * kH + 2 * kH) * 4 + kPBytes + kQBytes;
+constexpr size_t kRedBytes = (size_t)4 * kRows * 2 * 4;  // partial W3 sums [quarter][row][2]
+constexpr size_t kSmem = 1024 + kBBytes + kABytes + (size_t)(2 * kH + 2 * kH) * 4 + kPBytes + kQBytes + kRedBytes;
 static_assert(kSmem <= 232448, "shared memory");
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
@@ -58,6 +60,7 @@ __device__ __forceinline__ uint32_t b_off(int n, int g) { return (uint32_t)g * k
 __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInferParams p) {
   using namespace si;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = tid & (kRows - 1), cq = tid >> 7;  // tile row; quarter of the hidden columns
   const uint64_t wlim = wait_limit(p.status);  // read once: the waits below sit on critical paths
   const long Bv = p.rows / p.N;  // input vectors
   const long njt = (p.N + kTJ - 1) / kTJ, ntiles = ((Bv + kTB - 1) / kTB) * njt;
@@ -72,6 +75,7 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   float* w3s = b2s + kH;  // [2][kH]
   float* Ps = w3s + 2 * kH;          // [kTJ][kPPitch] rows of P of the tile's bit lines
   float* Qs = Ps + kTJ * kPPitch;    // [kTB][kH] rows of Q of the tile's vectors
+  float2* red = reinterpret_cast<float2*>(Qs + kTB * kH);  // [4][kRows] partial (s0, s1)
   // rows of P and Q of tile t into Ps, Qs (16-byte cp.async, zero fill past N or B)
   auto stage_rows = [&](long t) {
     const long b0 = (t / njt) * kTB, j0 = (t % njt) * kTJ;
@@ -119,15 +123,17 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   int issued = 0;  // tiles whose MMAs this block committed
   long prev = -1;
   // drain accumulator `buf` (tile t): b2, ReLU, BF16 rounding, W3, prediction
+  // (every thread takes part: the quarters' partial sums meet in shared memory)
   auto epilogue = [&](long t, int buf) {
-    const long b = (t / njt) * kTB + (tid >> 4), j = (t % njt) * kTJ + (tid & 15);
+    const long b = (t / njt) * kTB + (m >> 4), j = (t % njt) * kTJ + (m & 15);
     const bool real = b < Bv && j < p.N;
     const long r = b * p.N + j;
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll 1
-    for (int cb = 0; cb < kH; cb += 32) {
+    for (int cb = 64 * cq; cb < 64 * cq + 64; cb += 32) {
       float a[32];
-      umma::ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * kH + cb), a);
+      // warp w reads tensor-memory lanes 32 (w % 4) ..: rows m of this thread
+      umma::ld32(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * kH + cb), a);
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(a[q] + b2s[cb + q], 0.0f)));
@@ -135,7 +141,17 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
         s1 = fmaf(w3s[kH + cb + q], h, s1);
       }
     }
-    if (real) {
+    red[cq * kRows + m] = make_float2(s0, s1);
+    __syncthreads();
+    if (cq == 0) {
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        const float2 v = red[u * kRows + m];
+        s0 += v.x;
+        s1 += v.y;
+      }
+    }
+    if (cq == 0 && real) {
       const double ii = p.Iid[r];
       const float n0 = s0 + p.b3[0], n1 = s1 + p.b3[1];
       const double Ir = p.Iln[r] + ii * (p.mu + p.sigma * (double)n0);
@@ -150,20 +166,21 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
   for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int buf = issued & 1;
     // the previous tile's MMAs read the operand buffer: wait for them before regenerating it
-    if (issued >= 1)
+    if (issued >= 1 && tid == 0)
       ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
                              wlim, 20);
     cp_async_wait_all();  // this thread's copies of tile t's rows; the barrier shows everyone's
     if (__syncthreads_or(!ok)) break;
     umma::fence_after();
-    {  // operand of tile t: thread = row m = (vector qq, bit line rr), from the staged rows
-      const long b = (t / njt) * kTB + (tid >> 4), j = (t % njt) * kTJ + (tid & 15);
+    {  // operand of tile t: row m = (vector m / 16, bit line m % 16), core-matrix columns of this
+       // thread's quarter, from the staged rows
+      const long b = (t / njt) * kTB + (m >> 4), j = (t % njt) * kTJ + (m & 15);
       const bool real = b < Bv && j < p.N;
-      const float4* P4 = reinterpret_cast<const float4*>(Ps + (tid & 15) * kPPitch);
-      const float4* Q4 = reinterpret_cast<const float4*>(Qs + (tid >> 4) * kH);
+      const float4* P4 = reinterpret_cast<const float4*>(Ps + (m & 15) * kPPitch);
+      const float4* Q4 = reinterpret_cast<const float4*>(Qs + (m >> 4) * kH);
       const float4* C4 = reinterpret_cast<const float4*>(b1s);
 #pragma unroll
-      for (int g0 = 0; g0 < kH / 8; g0 += 4) {
+      for (int g0 = 8 * cq; g0 < 8 * cq + 8; g0 += 4) {
         float4 pa[8], qa[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -180,7 +197,7 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
           alignas(16) __nv_bfloat16 v[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(real ? fmaxf(z[e], 0.0f) : 0.0f);
-          *reinterpret_cast<uint4*>(As + a_off(tid, g)) = *reinterpret_cast<const uint4*>(v);
+          *reinterpret_cast<uint4*>(As + a_off(m, g)) = *reinterpret_cast<const uint4*>(v);
         }
       }
     }
@@ -203,14 +220,15 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
     prev = t;
   }
   if (ok && prev >= 0) {
-    ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
-                           wlim, 20);
+    if (tid == 0)
+      ok = mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status,
+                             wlim, 20);
     ok = !__syncthreads_or(!ok);
     umma::fence_after();
     if (ok) epilogue(prev, (issued - 1) & 1);
   }
   cp_async_wait_all();  // no copy may still be in flight when the block exits
-  if (!ok && issued >= 1)  // the last commit covers every MMA of this block: wait for it (bounded)
+  if (!ok && issued >= 1 && tid == 0)  // the last commit covers every MMA of this block (bounded wait)
     mbar_spin_bounded(&bar[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1), p.status, wlim, 20);
   umma::fence_before();
   __syncthreads();

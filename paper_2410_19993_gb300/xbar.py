@@ -52,7 +52,7 @@ class TileDesc(ctypes.Structure):
 
 
 OPTIONS = {"sweep_kernel": 0, "factor_kernel": 1, "algorithm": 2, "cr_products": 3, "wait_limit_ns": 4,
-           "orientation": 5}
+           "orientation": 5, "eager_assembly": 6}
 ALGORITHMS = {"thomas": 0, "cr": 1}
 ORIENTATIONS = {"auto": -1, "columns": 0, "rows": 1}
 _VALUE_NAMES = {"algorithm": ALGORITHMS, "orientation": ORIENTATIONS}

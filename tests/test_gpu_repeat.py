@@ -50,9 +50,10 @@ def test_repeated_fp64_solves_bit_identical():
             assert torch.equal(a, b)
 
 
-def test_set_conductances_then_factor_matches_fresh_handle():
-    """xbar_set_conductances assembles at once; a handle reused that way must give exactly what a
-    fresh handle of the same map gives."""
+@pytest.mark.parametrize("eager", [0, 1])
+def test_set_conductances_then_factor_matches_fresh_handle(eager):
+    """A handle reused through xbar_set_conductances (assembling there with XBAR_OPT_EAGER_ASSEMBLY,
+    else in the next factor) gives exactly what a fresh handle of the same map gives."""
     M, N, B = 256, 256, 1024
     G1, V = inputs.crossbar(M, N, B, seed=21)
     G2, _ = inputs.crossbar(M, N, 1, seed=22)
@@ -64,6 +65,7 @@ def test_set_conductances_then_factor_matches_fresh_handle():
     fresh.sync()
     fresh.destroy()
     reused = xbar.Crossbar.assemble(torch.from_numpy(G1).cuda(), *R)
+    reused.set_option("eager_assembly", eager)
     reused.factor("fp32_ir")
     reused.set_conductances(torch.from_numpy(G2).cuda())
     reused.factor("fp32_ir")
