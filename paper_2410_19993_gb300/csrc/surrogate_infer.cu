@@ -128,6 +128,13 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
     const long b = (t / njt) * kTB + (m >> 4), j = (t % njt) * kTJ + (m & 15);
     const bool real = b < Bv && j < p.N;
     const long r = b * p.N + j;
+    // the row's ideal and line-model currents, loaded before the accumulator reads so that their
+    // latency overlaps them
+    double ii = 0.0, il = 0.0;
+    if (cq == 0 && real) {
+      ii = p.Iid[r];
+      il = p.Iln[r];
+    }
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll 1
     for (int cb = 64 * cq; cb < 64 * cq + 64; cb += 32) {
@@ -152,9 +159,8 @@ __global__ void __launch_bounds__(si::kThreads, 1) surrogate_infer_kernel(SurInf
       }
     }
     if (cq == 0 && real) {
-      const double ii = p.Iid[r];
       const float n0 = s0 + p.b3[0], n1 = s1 + p.b3[1];
-      const double Ir = p.Iln[r] + ii * (p.mu + p.sigma * (double)n0);
+      const double Ir = il + ii * (p.mu + p.sigma * (double)n0);
       const double e = p.cal * p.sigma * (double)expf(n1) * fabs(ii) / fmax(fabs(Ir), 1e-300);
       p.I[r] = Ir;
       if (p.est) p.est[r] = e;
