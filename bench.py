@@ -339,6 +339,9 @@ def run_xbar(args):
         def step_e2e():  # the same two-map schedule with host buffers
             k = pipe["k"]
             xbs[(k + 1) % 2].set_conductances(Gh)
+            assembled = torch.cuda.Event()
+            assembled.record(streams[(k + 1) % 2])
+            streams[k % 2].wait_event(assembled)
             xbs[(k + 1) % 2].factor("fp32_ir")
             xbs[k % 2].solve(Vh, Ih, tol=TOL, max_iter=10)
             pipe["k"] = k + 1

@@ -1145,6 +1145,9 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
       if (!(G[k] >= 0.0) || !isfinite(G[k])) return fail(XBAR_EINVAL, "G[%zu]=%g must be finite and >= 0", k, G[k]);
     XB_CUDA(ensure(h->A, h->sV, std::max(h->sV.bytes, n * 8)));
     XB_CUDA(cudaMemcpyAsync(h->sV.p, G, n * 8, cudaMemcpyHostToDevice, h->st));
+    // G is read before the call returns; the kernels below stay asynchronous (a later xbar_solve
+    // refills the staging buffer on the same stream, after they have read it)
+    XB_CUDA(cudaStreamSynchronize(h->st));
     Gd = (const double*)h->sV.p;
   }
   h->factored = 0;
@@ -1161,7 +1164,6 @@ extern "C" xbar_status xbar_set_conductances(xbar_t h, const double* G) {
       h->assembled = 1;
     }
   }
-  if (!gdev) XB_CUDA(cudaStreamSynchronize(h->st));  // staging buffer is reused by xbar_solve
   return XBAR_OK;
 }
 
