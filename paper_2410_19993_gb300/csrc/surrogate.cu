@@ -325,11 +325,95 @@ __device__ __forceinline__ void bl_solve(float* f, const float* g, const float* 
   }
 }
 
+// Every chain sweep below is a first-order recurrence x_t = a_t x_{t-1} + b_t with a_t >= 0 (and
+// b_t >= 0 for the unit-input fields), i.e. a chain of affine maps x -> a x + b.  Their composition
+// is again affine, (a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2), so a group of kSegL lanes takes one
+// chain: each lane composes the maps of its segment, a scan over the group composes the segments,
+// and each lane walks its own segment from the value the scan gives at its start.  A segment is S
+// elements long with S = 8 or 24 (mod 32): with the [j][pitch] layout at pitch = M + 1 = 1 (mod 32)
+// (M = 128 and the like), lane l of the group of chain c then uses bank (c + 8 l' + step) mod 32 for
+// a permutation l' of 0..3, so the 32 lanes of a warp (8 chains x 4 lanes) hit 32 different banks,
+// along a column (consecutive t) and along a row (stride pitch) alike.
+constexpr int kSegL = 4;
+__device__ __forceinline__ int seg_len(int n) {
+  int S = (n + kSegL - 1) / kSegL;
+  const int r = S & 31;
+  S += r <= 8 ? 8 - r : (r <= 24 ? 24 - r : 40 - r);
+  return S;
+}
+template <typename AB, typename ST>
+__device__ __forceinline__ void seg_chain(int n, float x_init, AB ab, ST st) {
+  const int l = threadIdx.x & (kSegL - 1);
+  const int S = seg_len(n);
+  const int t0 = min(l * S, n), t1 = min(t0 + S, n);
+  float A = 1.0f, B = 0.0f;  // this segment's maps composed
+  for (int t = t0; t < t1; ++t) {
+    float a, b;
+    ab(t, a, b);
+    B = fmaf(a, B, b);
+    A *= a;
+  }
+#pragma unroll
+  for (int d = 1; d < kSegL; d <<= 1) {  // inclusive scan: this segment after the earlier ones
+    const float Ay = __shfl_up_sync(0xffffffffu, A, d, kSegL), By = __shfl_up_sync(0xffffffffu, B, d, kSegL);
+    if (l >= d) {
+      B = fmaf(A, By, B);
+      A *= Ay;
+    }
+  }
+  const float Ae = __shfl_up_sync(0xffffffffu, A, 1, kSegL), Be = __shfl_up_sync(0xffffffffu, B, 1, kSegL);
+  float x = l == 0 ? x_init : fmaf(Ae, x_init, Be);  // the value entering this segment
+  for (int t = t0; t < t1; ++t) {
+    float a, b;
+    ab(t, a, b);
+    x = fmaf(a, x, b);
+    st(t, x);
+  }
+}
+// Word line i (as wl_solve), the group's chain; n = 0 for a group without a line.
+__device__ __forceinline__ void wl_solve_seg(float* f, const float* g, const float* d, int pitch, int i, int n,
+                                             bool src, float gs, float gw) {
+  // back: t_j = (r_j + g_w t_{j+1}) / D_j, walked as t = n-1-j
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      const int o = (n - 1 - t) * pitch + i;
+      float r = g[o] * f[o];
+      if (src && t == n - 1) r += gs;
+      a = gw * d[o];
+      b = r * d[o];
+    }, [&](int t, float x) { f[(n - 1 - t) * pitch + i] = x; });
+  __syncwarp();
+  // forward: w_j = (g_w / D_j) w_{j-1} + t_j, w_0 = t_0
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      const int o = t * pitch + i;
+      a = t == 0 ? 0.0f : gw * d[o];
+      b = f[o];
+    }, [&](int t, float x) { f[t * pitch + i] = x; });
+}
+// Bit line j (as bl_solve), the group's chain; n = 0 for a group without a line.
+__device__ __forceinline__ void bl_solve_seg(float* f, const float* g, const float* e, int pitch, int j, int n,
+                                             float gb) {
+  float* fj = f + j * pitch;
+  const float* gj = g + j * pitch;
+  const float* ej = e + j * pitch;
+  // forward: s_i = (r_i + g_b s_{i-1}) / E_i
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      a = gb * ej[t];
+      b = gj[t] * fj[t] * ej[t];
+    }, [&](int t, float x) { fj[t] = x; });
+  __syncwarp();
+  // back: x_i = (g_b / E_i) x_{i+1} + s_i, walked as t = n-1-i, x_{n-1} = s_{n-1}
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      const int i = n - 1 - t;
+      a = t == 0 ? 0.0f : gb * ej[i];
+      b = fj[i];
+    }, [&](int t, float x) { fj[n - 1 - t] = x; });
+}
+
 // The whole line model of one unit input k in one block.  Shared memory holds the response field,
 // G, and one per-map factor array at a time (bit-line pivots, word-line pivots, sense weights),
 // all [N][M+1]: the odd pitch keeps both the row walks and the column walks free of bank
 // conflicts, and every chain step is a shared-memory access.  Pass 0 is tau in row k.
-__global__ void line_smem_kernel(const float* __restrict__ Gf, const float* __restrict__ wl,
+__global__ void __launch_bounds__(512, 1) line_smem_kernel(const float* __restrict__ Gf, const float* __restrict__ wl,
                                  const float* __restrict__ bl, const float* __restrict__ xg,
                                  const float* __restrict__ tau, int M, int N, int passes, float gs, float gw, float gb,
                                  double* __restrict__ T) {
@@ -347,23 +431,35 @@ __global__ void line_smem_kernel(const float* __restrict__ Gf, const float* __re
   stage(Gs, Gf);
   stage_block(Fs, M * N, [&](int t) { return t % M == k ? tau[t] : 0.0f; },
               [&](int t) { return (t / M) * P + t % M; });
+  // kSegL lanes per chain; every lane of the block runs the same number of rounds (the scans
+  // shuffle across the group), lanes of a group past the last chain with n = 0
+  const int groups = blockDim.x / kSegL, grp = threadIdx.x / kSegL;
   for (int p = 1; p < passes; ++p) {
     stage(As, bl);
     __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) bl_solve(Fs, Gs, As, P, j, M, gb);
+    for (int j0 = 0; j0 < N; j0 += groups) {
+      const int j = j0 + grp;
+      bl_solve_seg(Fs, Gs, As, P, j < N ? j : 0, j < N ? M : 0, gb);
+    }
     __syncthreads();
     stage(As, wl);
     __syncthreads();
-    for (int i = threadIdx.x; i < M; i += blockDim.x) wl_solve(Fs, Gs, As, P, i, N, i == k, gs, gw);
+    for (int i0 = 0; i0 < M; i0 += groups) {
+      const int i = i0 + grp;
+      wl_solve_seg(Fs, Gs, As, P, i < M ? i : 0, i < M ? N : 0, i == k, gs, gw);
+    }
     __syncthreads();
   }
   stage(As, xg);
   __syncthreads();
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+  for (int j0 = 0; j0 < N; j0 += groups) {  // T[j][k] = sum_i xg(i, j) w(i, j), kSegL lanes per sum
+    const int j = j0 + grp, l = threadIdx.x & (kSegL - 1), S = seg_len(M);
     float acc = 0.0f;
-#pragma unroll 8
-    for (int i = 0; i < M; ++i) acc = fmaf(As[j * P + i], Fs[j * P + i], acc);
-    T[(long)j * M + k] = acc;
+    if (j < N)
+      for (int i = min(l * S, M); i < min(l * S + S, M); ++i) acc = fmaf(As[j * P + i], Fs[j * P + i], acc);
+#pragma unroll
+    for (int d = kSegL / 2; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d, kSegL);
+    if (j < N && l == 0) T[(long)j * M + k] = acc;
   }
 }
 
@@ -931,7 +1027,7 @@ static xbar_status map_prep(xbar_surrogate_t s, const double* G, long sGi, long 
   prep_cols_kernel<<<(N + cb - 1) / cb, cb, smc, s->st>>>(Gf, M, N, gb, go, (float*)s->bl.p, (float*)s->xg.p);
   const size_t smem = 3 * (size_t)N * (M + 1) * 4;
   if (smem <= kLineSmemMax) {  // one block per unit input, everything in shared memory
-    const int threads = std::min(1024, round_up(std::max(M, N), 32));
+    const int threads = std::min(512, round_up(std::max(M, N) * kSegL, 32));  // kSegL lanes per chain
     XB_CUDA(cudaFuncSetAttribute(line_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     line_smem_kernel<<<M, threads, smem, s->st>>>(Gf, wl, bl, xg, tau, M, N, s->passes, gs, gw, gb, (double*)s->Tl.p);
   } else {  // the field in global memory, in chunks of inputs of at most 256 MiB
