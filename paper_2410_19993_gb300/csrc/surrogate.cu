@@ -164,168 +164,7 @@ __device__ __forceinline__ void stage_pitch2d(double* dst, const double* src, in
   }
 }
 
-// One thread per word line, blockDim.x (<= 32) lines per block; their conductances and pivots in
-// shared memory (pitch N + 1).  Dynamic shared memory: blockDim.x (N + 1) (8 + 4) bytes.
-__global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sGj, int M, int N, float gs, float gw,
-                                 double s_scale, double* __restrict__ Gt, float* __restrict__ St,
-                                 float* __restrict__ Gf, float* __restrict__ wl, float* __restrict__ tau) {
-  extern __shared__ double gsm[];
-  const int i0 = blockIdx.x * blockDim.x, rows = min((int)blockDim.x, M - i0), P = N + 1;
-  float* rsm = reinterpret_cast<float*>(gsm + blockDim.x * P);
-  const double* g0 = G + (long)i0 * sGi;
-  if (sGj == 1 && sGi == N && (N & 1) == 0 && (reinterpret_cast<uintptr_t>(g0) & 15) == 0)
-    stage_pitch2d(gsm, g0, N, rows, P);  // contiguous rows: 16-byte loads
-  else if (sGj == 1)  // consecutive threads along a row
-    stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t / N) * sGi + t % N]; },
-                [&](int t) { return (t / N) * P + t % N; });
-  else           // consecutive threads down a column
-    stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t % rows) * sGi + (long)(t / rows) * sGj]; },
-                [&](int t) { return (t % rows) * P + t / rows; });
-  __syncthreads();
-  const int r = threadIdx.x;
-  if (r >= rows) return;
-  const int i = i0 + r;
-  const double* g = gsm + r * P;
-  float* rd = rsm + r * P;
-  // The suffix sums S are a network feature (rounded to BF16 there): an FP32 sum of positive
-  // terms is ample, and it keeps the FP64 pipe (1/64 of FP32 here) off this sequential loop; each
-  // conductance is converted to FP32 once.
-  float acc = 0.0f;
-  const float sc = (float)s_scale;
-  float a = 0.0f, b = 1.0f;  // delta = a / b
-  for (int j0 = N - 1; j0 >= 0; j0 -= kU) {
-    const int n = min(kU, j0 + 1);
-    float bj[kU], dj[kU], gf[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      if (u < n) {
-        const float gv = (float)g[j0 - u];
-        const float num = ((j0 - u) == 0 ? gs : gw) * b + gv * b + gw * a;  // D_j b_j
-        bj[u] = b;
-        dj[u] = num;
-        gf[u] = gv;
-        a = gv * b + gw * a;
-        b = num;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      if (u < n) {
-        const int j = j0 - u;
-        const long o = (long)j * M + i;
-        const float w = bj[u] / dj[u];
-        Gt[o] = g[j];
-        Gf[o] = gf[u];
-        acc += gf[u];
-        St[o] = acc * sc;
-        wl[o] = w;
-        rd[j] = w;
-      }
-    }
-    rescale(a, b);
-  }
-  float t = gs * rd[0];  // forward: the first pass, driven at column 0
-  tau[i] = t;
-  for (int j = 1; j < N; ++j) {
-    t *= gw * rd[j];
-    tau[(long)j * M + i] = t;
-  }
-}
-
-// One thread per bit line, blockDim.x (<= 32) lines per block; their conductances and pivots in
-// shared memory (pitch M + 1).  Dynamic shared memory: 2 blockDim.x (M + 1) floats.
-__global__ void prep_cols_kernel(const float* __restrict__ Gf, int M, int N, float gb, float go,
-                                 float* __restrict__ bl, float* __restrict__ xg) {
-  extern __shared__ float csm[];
-  const int j0 = blockIdx.x * blockDim.x, cols = min((int)blockDim.x, N - j0), P = M + 1;
-  float* gsm = csm;                   // G, then g_o z G
-  float* esm = csm + blockDim.x * P;  // 1/E
-  const float* gf0 = Gf + (long)j0 * M;
-  if ((M & 3) == 0 && (reinterpret_cast<uintptr_t>(gf0) & 15) == 0)
-    stage_pitch4(gsm, gf0, M, cols, P);
-  else
-    stage_block(gsm, cols * M, [&](int t) { return Gf[(long)j0 * M + t]; },
-                [&](int t) { return (t / M) * P + t % M; });
-  __syncthreads();
-  const int c = threadIdx.x;
-  if (c < cols) {
-    float* g = gsm + c * P;
-    float* e = esm + c * P;
-    float a = 0.0f, cc = 1.0f;  // eps = a / cc
-    for (int i0 = 0; i0 < M; i0 += kU) {
-      const int n = min(kU, M - i0);
-      float ci[kU], ei[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        if (u < n) {
-          const float an = g[i0 + u] * cc + gb * a;
-          const float num = an + ((i0 + u) < M - 1 ? gb : go) * cc;  // E_i c_{i-1}
-          ci[u] = cc;
-          ei[u] = num;
-          a = an;
-          cc = num;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u)
-        if (u < n) e[i0 + u] = ci[u] / ei[u];
-      rescale(a, cc);
-    }
-    float x = e[M - 1];  // unit current at the bottom node: s_i = 0 above it
-    for (int i = M - 1; i >= 0; --i) {
-      g[i] = go * x * g[i];  // G is not read again
-      if (i > 0) x *= gb * e[i - 1];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < cols * M; t += blockDim.x) {  // coalesced: bl, xg are [N][M]
-    const int c2 = t / M, i = t - c2 * M;
-    bl[(long)(j0 + c2) * M + i] = esm[c2 * P + i];
-    xg[(long)(j0 + c2) * M + i] = gsm[c2 * P + i];
-  }
-}
-
-// Chain solves on an [N][pitch] field f (node (i, j) at f[j*pitch + i]).
-// Word line i: w = (L_i + diag G_i)^-1 (G_i o u + g_s [i == k] e_0), written over u (= f).
-__device__ __forceinline__ void wl_solve(float* f, const float* g, const float* d, int pitch, int i, int N, bool src,
-                                         float gs, float gw) {
-  float tn = 0.0f;
-#pragma unroll 4
-  for (int j = N - 1; j >= 0; --j) {  // t_j = (r_j + g_w t_{j+1}) / D_j
-    const int o = j * pitch + i;
-    float r = g[o] * f[o];
-    if (src && j == 0) r += gs;
-    tn = (r + gw * tn) * d[o];
-    f[o] = tn;
-  }
-  float w = f[i];
-#pragma unroll 4
-  for (int j = 1; j < N; ++j) {  // w_j = (g_w / D_j) w_{j-1} + t_j
-    const int o = j * pitch + i;
-    w = gw * d[o] * w + f[o];
-    f[o] = w;
-  }
-}
-// Bit line j: u = (K_j + diag G_j)^-1 (G_j o w), written over w (= f).
-__device__ __forceinline__ void bl_solve(float* f, const float* g, const float* e, int pitch, int j, int M, float gb) {
-  float* fj = f + j * pitch;
-  const float* gj = g + j * pitch;
-  const float* ej = e + j * pitch;
-  float sp = 0.0f;
-#pragma unroll 4
-  for (int i = 0; i < M; ++i) {  // s_i = (r_i + g_b s_{i-1}) / E_i
-    sp = (gj[i] * fj[i] + gb * sp) * ej[i];
-    fj[i] = sp;
-  }
-  float x = fj[M - 1];
-#pragma unroll 4
-  for (int i = M - 2; i >= 0; --i) {  // x_i = (g_b / E_i) x_{i+1} + s_i
-    x = gb * ej[i] * x + fj[i];
-    fj[i] = x;
-  }
-}
-
-// Every chain sweep below is a first-order recurrence x_t = a_t x_{t-1} + b_t with a_t >= 0 (and
+// Every chain sweep of the line model (and the bit-line weights of prep_cols) is a first-order recurrence x_t = a_t x_{t-1} + b_t with a_t >= 0 (and
 // b_t >= 0 for the unit-input fields), i.e. a chain of affine maps x -> a x + b.  Their composition
 // is again affine, (a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2), so a group of kSegL lanes takes one
 // chain: each lane composes the maps of its segment, a scan over the group composes the segments,
@@ -407,6 +246,227 @@ __device__ __forceinline__ void bl_solve_seg(float* f, const float* g, const flo
       a = t == 0 ? 0.0f : gb * ej[i];
       b = fj[i];
     }, [&](int t, float x) { fj[n - 1 - t] = x; });
+}
+
+// Word lines of the line model, blockDim.x / kSegL (<= 32) per block, kSegL lanes per line; their
+// conductances and pivots in shared memory (pitch N + 1).  Dynamic shared memory:
+// (blockDim.x / kSegL) (N + 1) (8 + 4) bytes.  Per line, from the far end j = N-1 down to j = 0:
+//   pivots: (a, b) <- [[g_w, G_j], [g_w, G_j + k_j]] (a, b) from (0, 1), k_j = g_w (g_s at j = 0),
+//           word-line ratio w_j = b_{j+1} / b_j (positive 2 x 2 maps, segmented scan as in prep_cols);
+//   suffix sums S_j = sum_{j' >= j} G_j' (a feature, rounded to BF16 by the network: FP32 is ample);
+//   forward: tau_0 = g_s w_0, tau_j = g_w w_j tau_{j-1}.
+__global__ void prep_rows_kernel(const double* __restrict__ G, long sGi, long sGj, int M, int N, float gs, float gw,
+                                 double s_scale, double* __restrict__ Gt, float* __restrict__ St,
+                                 float* __restrict__ Gf, float* __restrict__ wl, float* __restrict__ tau) {
+  extern __shared__ double gsm[];
+  const int lines = blockDim.x / kSegL;
+  const int i0 = blockIdx.x * lines, rows = min(lines, M - i0), P = N + 1;
+  float* rsm = reinterpret_cast<float*>(gsm + lines * P);
+  const double* g0 = G + (long)i0 * sGi;
+  if (sGj == 1 && sGi == N && (N & 1) == 0 && (reinterpret_cast<uintptr_t>(g0) & 15) == 0)
+    stage_pitch2d(gsm, g0, N, rows, P);  // contiguous rows: 16-byte loads
+  else if (sGj == 1)  // consecutive threads along a row
+    stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t / N) * sGi + t % N]; },
+                [&](int t) { return (t / N) * P + t % N; });
+  else           // consecutive threads down a column
+    stage_block(gsm, rows * N, [&](int t) { return G[(long)(i0 + t % rows) * sGi + (long)(t / rows) * sGj]; },
+                [&](int t) { return (t % rows) * P + t / rows; });
+  __syncthreads();
+  const int r = threadIdx.x / kSegL, l = threadIdx.x & (kSegL - 1);
+  const bool live = r < rows;
+  const int n = live ? N : 0;  // every lane takes part in the group's shuffles
+  const int i = i0 + (live ? r : 0);
+  const double* g = gsm + (live ? r : 0) * P;
+  float* rd = rsm + (live ? r : 0) * P;
+  {  // pivots, walked as t = N-1-j
+    const int S = seg_len(n), t0 = min(l * S, n), t1 = min(t0 + S, n);
+    auto kof = [&](int j) { return j == 0 ? gs : gw; };
+    float p00 = 1.0f, p01 = 0.0f, p10 = 0.0f, p11 = 1.0f;  // this segment's maps, latest on the left
+    for (int t = t0; t < t1; ++t) {
+      const int j = n - 1 - t;
+      const float gv = (float)g[j], gk = gv + kof(j);
+      const float n00 = gw * p00 + gv * p10, n01 = gw * p01 + gv * p11;
+      const float n10 = gw * p00 + gk * p10, n11 = gw * p01 + gk * p11;
+      int ex;
+      frexpf(fmaxf(fmaxf(n00, n01), fmaxf(n10, n11)), &ex);
+      p00 = ldexpf(n00, -ex);
+      p01 = ldexpf(n01, -ex);
+      p10 = ldexpf(n10, -ex);
+      p11 = ldexpf(n11, -ex);
+    }
+#pragma unroll
+    for (int d = 1; d < kSegL; d <<= 1) {  // inclusive scan: this segment's maps after the earlier ones
+      const float y00 = __shfl_up_sync(0xffffffffu, p00, d, kSegL), y01 = __shfl_up_sync(0xffffffffu, p01, d, kSegL);
+      const float y10 = __shfl_up_sync(0xffffffffu, p10, d, kSegL), y11 = __shfl_up_sync(0xffffffffu, p11, d, kSegL);
+      if (l >= d) {
+        const float n00 = p00 * y00 + p01 * y10, n01 = p00 * y01 + p01 * y11;
+        const float n10 = p10 * y00 + p11 * y10, n11 = p10 * y01 + p11 * y11;
+        int ex;
+        frexpf(fmaxf(fmaxf(n00, n01), fmaxf(n10, n11)), &ex);
+        p00 = ldexpf(n00, -ex);
+        p01 = ldexpf(n01, -ex);
+        p10 = ldexpf(n10, -ex);
+        p11 = ldexpf(n11, -ex);
+      }
+    }
+    float a = __shfl_up_sync(0xffffffffu, p01, 1, kSegL), b = __shfl_up_sync(0xffffffffu, p11, 1, kSegL);
+    if (l == 0) {
+      a = 0.0f;
+      b = 1.0f;
+    }
+    rescale(a, b);
+    for (int t = t0; t < t1; ++t) {
+      const int j = n - 1 - t;
+      const float gv = (float)g[j];
+      const float num = kof(j) * b + gv * b + gw * a;  // D_j b_j
+      const float w = b / num;
+      const long o = (long)j * M + i;
+      Gt[o] = g[j];
+      Gf[o] = gv;
+      wl[o] = w;
+      rd[j] = w;
+      a = gv * b + gw * a;
+      b = num;
+      rescale(a, b);
+    }
+  }
+  // suffix sums of G (FP32), walked as t = N-1-j
+  const float sc = (float)s_scale;
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      a = 1.0f;
+      b = (float)g[n - 1 - t];
+    }, [&](int t, float x) { St[(long)(n - 1 - t) * M + i] = x * sc; });
+  __syncwarp();
+  // forward: the first pass, driven at column 0
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      a = t == 0 ? 0.0f : gw * rd[t];
+      b = t == 0 ? gs * rd[0] : 0.0f;
+    }, [&](int t, float x) { tau[(long)t * M + i] = x; });
+}
+
+// Bit lines of the line model, blockDim.x / kSegL (<= 32) per block, kSegL lanes per line (segmented
+// scans as in the line model below); their conductances and pivots in shared memory (pitch M + 1).
+// Dynamic shared memory: 2 (blockDim.x / kSegL) (M + 1) floats.
+//   pivots: (a, c) <- [[g_b, G_i], [g_b, G_i + k_i]] (a, c) from (0, 1), k_i = g_b (g_o at the
+//           bottom), 1/E_i = c_{i-1} / c_i (a chain of positive 2 x 2 maps: each lane composes its
+//           segment's, a scan over the group composes the segments, powers-of-two rescaling);
+//   sense weights: x_{M-1} = 1/E_{M-1}, x_i = g_b (1/E_i) x_{i+1}, stored as g_o x_i G_i.
+__global__ void prep_cols_kernel(const float* __restrict__ Gf, int M, int N, float gb, float go,
+                                 float* __restrict__ bl, float* __restrict__ xg) {
+  extern __shared__ float csm[];
+  const int lines = blockDim.x / kSegL;
+  const int j0 = blockIdx.x * lines, cols = min(lines, N - j0), P = M + 1;
+  float* gsm = csm;              // G, then g_o x G
+  float* esm = csm + lines * P;  // 1/E
+  const float* gf0 = Gf + (long)j0 * M;
+  if ((M & 3) == 0 && (reinterpret_cast<uintptr_t>(gf0) & 15) == 0)
+    stage_pitch4(gsm, gf0, M, cols, P);
+  else
+    stage_block(gsm, cols * M, [&](int t) { return Gf[(long)j0 * M + t]; },
+                [&](int t) { return (t / M) * P + t % M; });
+  __syncthreads();
+  const int c = threadIdx.x / kSegL, l = threadIdx.x & (kSegL - 1);
+  const int n = c < cols ? M : 0;  // every lane takes part in the group's shuffles
+  float* g = gsm + (c < cols ? c : 0) * P;
+  float* e = esm + (c < cols ? c : 0) * P;
+  {
+    const int S = seg_len(n), t0 = min(l * S, n), t1 = min(t0 + S, n);
+    auto kof = [&](int i) { return i < M - 1 ? gb : go; };
+    float p00 = 1.0f, p01 = 0.0f, p10 = 0.0f, p11 = 1.0f;  // this segment's maps, latest on the left
+    for (int i = t0; i < t1; ++i) {
+      const float gv = g[i], gk = gv + kof(i);
+      const float n00 = gb * p00 + gv * p10, n01 = gb * p01 + gv * p11;
+      const float n10 = gb * p00 + gk * p10, n11 = gb * p01 + gk * p11;
+      int ex;
+      frexpf(fmaxf(fmaxf(n00, n01), fmaxf(n10, n11)), &ex);
+      p00 = ldexpf(n00, -ex);
+      p01 = ldexpf(n01, -ex);
+      p10 = ldexpf(n10, -ex);
+      p11 = ldexpf(n11, -ex);
+    }
+#pragma unroll
+    for (int d = 1; d < kSegL; d <<= 1) {  // inclusive scan: this segment's maps after the earlier ones
+      const float y00 = __shfl_up_sync(0xffffffffu, p00, d, kSegL), y01 = __shfl_up_sync(0xffffffffu, p01, d, kSegL);
+      const float y10 = __shfl_up_sync(0xffffffffu, p10, d, kSegL), y11 = __shfl_up_sync(0xffffffffu, p11, d, kSegL);
+      if (l >= d) {
+        const float n00 = p00 * y00 + p01 * y10, n01 = p00 * y01 + p01 * y11;
+        const float n10 = p10 * y00 + p11 * y10, n11 = p10 * y01 + p11 * y11;
+        int ex;
+        frexpf(fmaxf(fmaxf(n00, n01), fmaxf(n10, n11)), &ex);
+        p00 = ldexpf(n00, -ex);
+        p01 = ldexpf(n01, -ex);
+        p10 = ldexpf(n10, -ex);
+        p11 = ldexpf(n11, -ex);
+      }
+    }
+    // (a, c) entering the segment: the earlier segments' maps applied to (0, 1)
+    float a = __shfl_up_sync(0xffffffffu, p01, 1, kSegL), cc = __shfl_up_sync(0xffffffffu, p11, 1, kSegL);
+    if (l == 0) {
+      a = 0.0f;
+      cc = 1.0f;
+    }
+    rescale(a, cc);
+    for (int i = t0; i < t1; ++i) {
+      const float an = g[i] * cc + gb * a;
+      const float num = an + kof(i) * cc;  // E_i c_{i-1}
+      e[i] = cc / num;
+      a = an;
+      cc = num;
+      rescale(a, cc);
+    }
+  }
+  __syncwarp();
+  // sense weights, walked from the bottom node (t = M-1-i)
+  seg_chain(n, 0.0f, [&](int t, float& a, float& b) {
+      a = t == 0 ? 0.0f : gb * e[n - 1 - t];
+      b = t == 0 ? e[n - 1] : 0.0f;
+    }, [&](int t, float x) { g[n - 1 - t] = go * x * g[n - 1 - t]; });
+  __syncthreads();
+  for (int t = threadIdx.x; t < cols * M; t += blockDim.x) {  // coalesced: bl, xg are [N][M]
+    const int c2 = t / M, i = t - c2 * M;
+    bl[(long)(j0 + c2) * M + i] = esm[c2 * P + i];
+    xg[(long)(j0 + c2) * M + i] = gsm[c2 * P + i];
+  }
+}
+
+// Chain solves on an [N][pitch] field f (node (i, j) at f[j*pitch + i]).
+// Word line i: w = (L_i + diag G_i)^-1 (G_i o u + g_s [i == k] e_0), written over u (= f).
+__device__ __forceinline__ void wl_solve(float* f, const float* g, const float* d, int pitch, int i, int N, bool src,
+                                         float gs, float gw) {
+  float tn = 0.0f;
+#pragma unroll 4
+  for (int j = N - 1; j >= 0; --j) {  // t_j = (r_j + g_w t_{j+1}) / D_j
+    const int o = j * pitch + i;
+    float r = g[o] * f[o];
+    if (src && j == 0) r += gs;
+    tn = (r + gw * tn) * d[o];
+    f[o] = tn;
+  }
+  float w = f[i];
+#pragma unroll 4
+  for (int j = 1; j < N; ++j) {  // w_j = (g_w / D_j) w_{j-1} + t_j
+    const int o = j * pitch + i;
+    w = gw * d[o] * w + f[o];
+    f[o] = w;
+  }
+}
+// Bit line j: u = (K_j + diag G_j)^-1 (G_j o w), written over w (= f).
+__device__ __forceinline__ void bl_solve(float* f, const float* g, const float* e, int pitch, int j, int M, float gb) {
+  float* fj = f + j * pitch;
+  const float* gj = g + j * pitch;
+  const float* ej = e + j * pitch;
+  float sp = 0.0f;
+#pragma unroll 4
+  for (int i = 0; i < M; ++i) {  // s_i = (r_i + g_b s_{i-1}) / E_i
+    sp = (gj[i] * fj[i] + gb * sp) * ej[i];
+    fj[i] = sp;
+  }
+  float x = fj[M - 1];
+#pragma unroll 4
+  for (int i = M - 2; i >= 0; --i) {  // x_i = (g_b / E_i) x_{i+1} + s_i
+    x = gb * ej[i] * x + fj[i];
+    fj[i] = x;
+  }
 }
 
 // The whole line model of one unit input k in one block.  Shared memory holds the response field,
@@ -1021,10 +1081,10 @@ static xbar_status map_prep(xbar_surrogate_t s, const double* G, long sGi, long 
   if (smr > kPrepSmemMax || smc > kPrepSmemMax) return set_error(XBAR_EINVAL, "map too large for the line model");
   XB_CUDA(cudaFuncSetAttribute(prep_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
   XB_CUDA(cudaFuncSetAttribute(prep_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-  prep_rows_kernel<<<(M + rb - 1) / rb, rb, smr, s->st>>>(G, sGi, sGj, M, N, gs, gw, 1.0 / (N * s->gs), (double*)s->Gt.p,
+  prep_rows_kernel<<<(M + rb - 1) / rb, rb * kSegL, smr, s->st>>>(G, sGi, sGj, M, N, gs, gw, 1.0 / (N * s->gs), (double*)s->Gt.p,
                                                     (float*)s->St.p, (float*)s->Gf.p, (float*)s->wl.p,
                                                     (float*)s->tau.p);
-  prep_cols_kernel<<<(N + cb - 1) / cb, cb, smc, s->st>>>(Gf, M, N, gb, go, (float*)s->bl.p, (float*)s->xg.p);
+  prep_cols_kernel<<<(N + cb - 1) / cb, cb * kSegL, smc, s->st>>>(Gf, M, N, gb, go, (float*)s->bl.p, (float*)s->xg.p);
   const size_t smem = 3 * (size_t)N * (M + 1) * 4;
   if (smem <= kLineSmemMax) {  // one block per unit input, everything in shared memory
     const int threads = std::min(512, round_up(std::max(M, N) * kSegL, 32));  // kSegL lanes per chain
