@@ -600,34 +600,56 @@ __global__ void infer_gt32_kernel(const double* Gt, const double* Tl, int M, int
 // relative error, ~1e-7, is far below the network's); one block per kVB input vectors, so each
 // load of G and T_line serves kVB vectors
 constexpr int kVB = 8;
-__global__ void infer_currents_kernel(const double* V, const float* G32, const float* T32, int M, int N, int B,
-                                      double* Iid, double* Iln) {
-  extern __shared__ float vs[];  // [kVB][M]
+constexpr int kIP = 4;  // parts of the row range per column (partial sums combined in shared memory)
+__global__ void __launch_bounds__(128 * kIP) infer_currents_kernel(const double* V, const float* G32, const float* T32,
+                                                                   int M, int N, int B, double* Iid, double* Iln) {
+  extern __shared__ float vs[];  // [kVB][M], then partial sums [kIP - 1][2 kVB][128]
+  float* part = vs + kVB * M;
   const int b0 = blockIdx.x * kVB;
   for (int t = threadIdx.x; t < kVB * M; t += blockDim.x) {
     const int u = t / M, i = t - u * M;
     vs[t] = b0 + u < B ? (float)V[(long)(b0 + u) * M + i] : 0.0f;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+  const int jl = threadIdx.x & 127, q = threadIdx.x >> 7;  // column within the pass, part of the rows
+  const int i0 = q * M / kIP, i1 = (q + 1) * M / kIP;
+  for (int j0 = 0; j0 < N; j0 += 128) {
+    const int j = j0 + jl;
     float a[kVB], c[kVB];
 #pragma unroll
     for (int u = 0; u < kVB; ++u) a[u] = c[u] = 0.0f;
+    if (j < N) {
 #pragma unroll 4
-    for (int i = 0; i < M; ++i) {
-      const float g = G32[(long)i * N + j], t = T32[(long)i * N + j];
+      for (int i = i0; i < i1; ++i) {
+        const float g = G32[(long)i * N + j], t = T32[(long)i * N + j];
 #pragma unroll
-      for (int u = 0; u < kVB; ++u) {
-        a[u] = fmaf(vs[u * M + i], g, a[u]);
-        c[u] = fmaf(vs[u * M + i], t, c[u]);
+        for (int u = 0; u < kVB; ++u) {
+          a[u] = fmaf(vs[u * M + i], g, a[u]);
+          c[u] = fmaf(vs[u * M + i], t, c[u]);
+        }
       }
     }
+    if (q > 0)
 #pragma unroll
-    for (int u = 0; u < kVB; ++u)
-      if (b0 + u < B) {
-        Iid[(long)(b0 + u) * N + j] = a[u];
-        Iln[(long)(b0 + u) * N + j] = c[u];
+      for (int u = 0; u < kVB; ++u) {
+        part[((q - 1) * 2 * kVB + u) * 128 + jl] = a[u];
+        part[((q - 1) * 2 * kVB + kVB + u) * 128 + jl] = c[u];
       }
+    __syncthreads();
+    if (q == 0 && j < N) {
+#pragma unroll
+      for (int u = 0; u < kVB; ++u) {
+        for (int p = 0; p < kIP - 1; ++p) {
+          a[u] += part[(p * 2 * kVB + u) * 128 + jl];
+          c[u] += part[(p * 2 * kVB + kVB + u) * 128 + jl];
+        }
+        if (b0 + u < B) {
+          Iid[(long)(b0 + u) * N + j] = a[u];
+          Iln[(long)(b0 + u) * N + j] = c[u];
+        }
+      }
+    }
+    __syncthreads();  // the partial sums are read before the next pass writes them
   }
 }
 
@@ -1257,7 +1279,9 @@ static xbar_status predict_map(xbar_surrogate_t s, const double* G, long sGi, lo
                                                                            (__nv_bfloat16*)s->xv.p);
   infer_gt32_kernel<<<(unsigned)(((long)M * N + 255) / 256), 256, 0, s->st>>>(
       (const double*)s->Gt.p, (const double*)s->Tl.p, M, N, (float*)s->g32.p, (float*)s->t32.p);
-  infer_currents_kernel<<<(B + kVB - 1) / kVB, 128, kVB * M * sizeof(float), s->st>>>(
+  const size_t ic_smem = ((size_t)kVB * M + (size_t)(kIP - 1) * 2 * kVB * 128) * sizeof(float);
+  XB_CUDA(cudaFuncSetAttribute(infer_currents_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ic_smem));
+  infer_currents_kernel<<<(B + kVB - 1) / kVB, 128 * kIP, ic_smem, s->st>>>(
       V, (const float*)s->g32.p, (const float*)s->t32.p, M, N, B, (double*)s->Iid.p, (double*)s->Iln.p);
   XB_CUDA(cudaGetLastError());
   GemmBf16Params g;
