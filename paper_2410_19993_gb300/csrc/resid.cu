@@ -16,7 +16,8 @@
 // 256 x 256, against the 1e-8 target.
 //
 // One thread per (column j, input vector b); consecutive threads take consecutive b, so every
-// access to the [N][Mp][Bpad] arrays is coalesced.  Loops run along the chain i.
+// access to the [N][Mp][Bpad] arrays is coalesced.  Loops run along the chain i (the residual in
+// segments of rows, see resid_kernel).
 #include <math.h>
 
 #include <algorithm>

@@ -5,9 +5,10 @@
 // with the bit lines at ground, giving word-line voltage ratios tau(i, j); then every bit line is
 // solved alone with device i driven by V_i tau(i, j).  It is linear in V:
 //     I_line = V T_line,   T_line(i, j) = tau(i, j) G(i, j) g_o x_j(i),
-// x_j solving bit line j's chain for a unit current at its bottom node.  Both chains are walked
-// once from their open end with subtraction-free ratio recurrences in FP32 (one thread per line
-// for the per-map factors; the unit-input responses walk the chains in shared memory).
+// x_j solving bit line j's chain for a unit current at its bottom node.  Both chains are factored
+// from their open end with subtraction-free ratio recurrences in FP32, and every chain sweep (the
+// per-map factors and the unit-input responses, in shared memory) is a chain of positive affine or
+// 2 x 2 linear maps, run as a segmented scan by four lanes per line.
 //
 // Network: for bit line j of map G and input vector V it reads 3M features
 //     x = [ G(:,j) / g_scale,  V / v_scale,  S(:,j) / (N g_scale) ],  S(i, j) = sum_{l>=j} G(i, l)
